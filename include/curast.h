@@ -1,0 +1,239 @@
+/*
+ * curast.h -- C ABI of the GB300 visibility-buffer rasterizer.
+ *
+ * The calls follow the paper's statement of the problem (Schuetz, Lipp,
+ * Kristmann, Wimmer: "CuRast: Cuda-Based Software Rasterization for Billions
+ * of Triangles"): indexed meshes and their instances (Section 3, "Method";
+ * Section 3.5 "Instancing") are rasterized by brute force into a 64-bit
+ * visibility buffer holding 28 depth bits and a 36-bit global triangle id
+ * (Section 3.1 "Rasterization"), which a screen pass then resolves into
+ * colours (Section 3.4).
+ *
+ * Conventions for every call
+ *   - Pointers marked "device" are CUDA device pointers on the context's
+ *     device; "host" pointers are ordinary memory read during the call.
+ *   - Matrices are 16 host floats, row-major (m[4*row + col]).  view and
+ *     model must be affine (last row 0 0 0 1).  proj must be a symmetric
+ *     perspective matrix: proj[1]=proj[2]=proj[3]=proj[4]=proj[6]=proj[7]=
+ *     proj[8]=proj[9]=0, last row (0, 0, -1, 0); the projection vector of
+ *     Eq. 2 is read off it as fx = proj[0] (f/aspect), fy = proj[5] (f), and
+ *     the near plane as proj[11] / (proj[10] - 1) (double, rounded to float).
+ *   - Images (visibility buffers, colours, gradients) are W x H pixels,
+ *     row-major, row 0 = the BOTTOM row (y up), pixel (x, y) at y * W + x.
+ *     1 <= W, H <= 16384.
+ *   - A visibility word is (depth28 << 36) | id, where depth28 is the FP32
+ *     bit pattern of the pixel's positive linear view depth shifted right by
+ *     3 (sign and 3 low mantissa bits dropped) and id is the global triangle
+ *     id; an empty pixel holds 0xFFFFFFFFFFFFFFFF.
+ *   - Global id of triangle t of instance i = base[i] + t, where base is the
+ *     exclusive prefix sum of the triangle counts of all instances in the
+ *     order they were added (Section 3, host frame setup; Section 3.4).
+ *   - Work is enqueued on the given CUDA stream (NULL = legacy default
+ *     stream) and the call returns without waiting for the GPU.  Inputs
+ *     must stay valid and unmodified until the stream reaches the work.
+ *   - Every call returns a status; no C++ exception crosses this boundary.
+ *     Conditions found on the device (an index out of range when checking
+ *     is on, a queue overflow) are latched in the context and reported by
+ *     curast_sync.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef CURAST_H
+#define CURAST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t curast_status;
+#define CURAST_OK                        0
+#define CURAST_ERR_INVALID_ARG          -1  /* null pointer, bad size, bad id  */
+#define CURAST_ERR_OUT_OF_MEMORY        -2  /* a context allocation failed      */
+#define CURAST_ERR_ID_SPACE_OVERFLOW    -3  /* total triangles > 2^36 - 1       */
+#define CURAST_ERR_INDEX_OUT_OF_RANGE   -4  /* device check found index >= V    */
+#define CURAST_ERR_DEVICE_TIMEOUT       -5  /* a bounded device wait gave up    */
+#define CURAST_ERR_CUDA                 -6  /* a CUDA runtime call failed       */
+#define CURAST_ERR_NOT_AFFINE           -7  /* view/model last row not 0 0 0 1  */
+#define CURAST_ERR_BAD_CAMERA           -8  /* proj is not symmetric perspective*/
+#define CURAST_ERR_NOT_BUILT            -9  /* no kernel image for this device  */
+
+typedef struct curast_ctx curast_ctx;
+
+/* A CUDA stream handle (cudaStream_t) passed as an opaque pointer. */
+typedef void *curast_stream;
+
+/* One view of a batched render: camera, size and its visibility buffer
+ * (device, W*H words, caller-owned). */
+typedef struct {
+    float view[16];
+    float proj[16];
+    int32_t W, H;
+    uint64_t *vis;
+} curast_view;
+
+/* Tunables.  None of them changes a visibility buffer: every triangle is
+ * covered by the same exact rule whichever stage rasterizes it. */
+typedef struct {
+    uint32_t stage1_max_pixels;  /* stage 1 rasterizes bbox <= this (paper: 128), 1..1024   */
+    uint32_t stage2_max_pixels;  /* stage 2 rasterizes bbox <= this (paper: 4096), >= 32     */
+    uint32_t tile_log2;          /* stage-3 tile side 2^k px (paper: 64 -> 6), 4..7          */
+    uint32_t stage1_tri_per_thread; /* triangles per thread per stage-1 work grab, 1..32     */
+    uint32_t pairs_per_segment;  /* instance-view pairs one stage-1 work item loops over     */
+    uint64_t queue1_capacity;    /* stage 1 -> 2 queue entries; overflow is rasterized in place */
+    uint64_t queue2_capacity;    /* stage 2 -> 3 tile parts;   overflow is rasterized in place */
+    uint32_t check_indices;      /* 1: bounds-check every index on the device               */
+    uint32_t collect_stats;      /* 1: count culled / forwarded triangles (slower)           */
+} curast_config;
+
+/* Counters read back by curast_sync.  Stats fields are filled only when
+ * collect_stats is on. */
+typedef struct {
+    uint64_t triangles_in;       /* triangle x (instance, view) pairs entering stage 1 */
+    uint64_t culled_clip;        /* whole triangle beyond one clip plane               */
+    uint64_t culled_backface;    /* area <= 0 after snapping (stage 1)                 */
+    uint64_t culled_tiny;        /* bbox holds no pixel centre (stage 1)               */
+    uint64_t stage1_rasterized;
+    uint64_t queued_stage2;
+    uint64_t stage2_rasterized;  /* sub-triangles rasterized by stage 2                */
+    uint64_t queued_stage3;      /* tile parts                                          */
+    uint64_t queue1_overflow;    /* rasterized in place because queue 1 was full        */
+    uint64_t queue2_overflow;
+    uint32_t device_error;       /* nonzero: an index >= V was found (check_indices)    */
+    uint32_t reserved;
+} curast_stats;
+
+/* ------------------------------------------------------------ context --- */
+
+/* Creates a context on CUDA device `device`: queues, frame tables and the
+ * tuning state.  Fails with CURAST_ERR_NOT_BUILT when the library holds no
+ * kernels for that device (it is built for sm_103a only). */
+curast_status curast_create(curast_ctx **out, int device);
+
+/* Waits for the context's work and frees what the context allocated (never
+ * the caller's buffers).  NULL is ignored. */
+void curast_destroy(curast_ctx *ctx);
+
+const char *curast_status_string(curast_status s);
+
+curast_status curast_get_config(const curast_ctx *ctx, curast_config *out);
+/* Validates and installs a configuration; queue capacities are reallocated
+ * when they change. */
+curast_status curast_set_config(curast_ctx *ctx, const curast_config *cfg);
+
+/* ------------------------------------------------------- scene objects --- */
+
+/* Registers an indexed triangle mesh (Section 3: indexed meshes; Section
+ * 3.1: only indices and positions are read while rasterizing).
+ *   pos    device, V x 3 FP32 (x, y, z), 4-byte aligned
+ *   idx    device, T x 3 uint32 vertex indices, triangles wound CCW = front
+ *   rgba8  device, V x 4 bytes of vertex colour for curast_resolve, or NULL
+ *   flags  must be 0
+ * The buffers are BORROWED: they must stay allocated until curast_destroy;
+ * their contents may change between renders.  T may be 0. */
+curast_status curast_upload_mesh(curast_ctx *ctx, const float *pos, uint64_t V, const uint32_t *idx,
+                                 uint64_t T, const uint8_t *rgba8, uint32_t flags, uint32_t *mesh_id);
+
+/* Points a registered mesh at other buffers of the same V and T (e.g. new
+ * positions for the differentiable path).  NULL keeps the current one. */
+curast_status curast_update_mesh(curast_ctx *ctx, uint32_t mesh_id, const float *pos, const uint32_t *idx,
+                                 const uint8_t *rgba8);
+
+/* Adds an instance of a mesh with an affine model matrix (Section 3.5).
+ * Its ids start at the running total of triangles of the instances added
+ * before it.  Fails with CURAST_ERR_ID_SPACE_OVERFLOW when the total would
+ * exceed 2^36 - 1 triangles. */
+curast_status curast_add_instance(curast_ctx *ctx, uint32_t mesh_id, const float model[16],
+                                  uint32_t *instance_id);
+
+/* Removes all instances (meshes stay registered). */
+curast_status curast_clear_instances(curast_ctx *ctx);
+
+/* ------------------------------------------------------------ render --- */
+
+/* Fills a visibility buffer with 0xFF..FF (device, n words). */
+curast_status curast_clear(uint64_t *vis, uint64_t n, curast_stream stream);
+
+/* One frame of every instance into one view (Section 3: host setup, then
+ * stages 1, 2 and 3): clears vis, then for every triangle of every instance
+ * whose bounds intersect the view frustum keeps, per pixel, the minimum
+ * visibility word of the covered fragments.  vis: device, W*H words,
+ * caller-owned, 8-byte aligned. */
+curast_status curast_render(curast_ctx *ctx, const float view[16], const float proj[16], int W, int H,
+                            uint64_t *vis, curast_stream stream);
+
+/* Renders only the instances of one mesh into vis WITHOUT clearing it (the
+ * one-launch-per-mesh-per-view path the batched form is compared with). */
+curast_status curast_render_mesh(curast_ctx *ctx, uint32_t mesh_id, const float view[16],
+                                 const float proj[16], int W, int H, uint64_t *vis, curast_stream stream);
+
+/* Batched frame: every instance into every view in ONE persistent launch
+ * sequence (Section 3.1 "Looping Through Batches", Section 3.5 extended to
+ * several views: each triangle is loaded once and rasterized into every
+ * (instance, view) pair whose bounds meet that view).  Clears every view's
+ * buffer first.  With use_graph = 1 the launch sequence is captured once in
+ * a CUDA graph (re-captured when the views' sizes or buffers change) and
+ * replayed; the frame's matrices are uploaded before the replay.  The
+ * result is identical to curast_render per view. */
+curast_status curast_render_batch(curast_ctx *ctx, const curast_view *views, int n_views, int use_graph,
+                                  curast_stream stream);
+
+/* ------------------------------------------------------------ resolve --- */
+
+/* Screen pass (Section 3.4): per pixel, decode the id, find its instance by
+ * binary search of the prefix sum, fetch the triangle, intersect the pixel
+ * centre ray with it in view space and interpolate the RGBA8 vertex colours
+ * (c = byte / 255).  rgba_f32: device W*H*4 floats or NULL; rgba8: device
+ * W*H*4 bytes (rint(clamp(c, 0, 1) * 255)) or NULL.  Empty pixels, and
+ * pixels of meshes without colours, get all zeros.  The camera must be the
+ * one vis was rendered with, and the instance list unchanged since. */
+curast_status curast_resolve(curast_ctx *ctx, const float view[16], const float proj[16], int W, int H,
+                             const uint64_t *vis, float *rgba_f32, uint8_t *rgba8, curast_stream stream);
+
+/* --------------------------------------------------- differentiable step --- */
+
+/* Forward of the differentiable interpolation (perspective-correct
+ * barycentrics of Section 3.4 applied to a float attribute): for pixels
+ * whose triangle belongs to an instance of mesh_id,
+ * out[p] = sum_k b_k(p) attr[v_k]; other pixels get 0.
+ *   pos   device V x 3 positions to use instead of the registered ones, or NULL
+ *   attr  device V x C floats (1 <= C <= 16); out device W*H*C floats. */
+curast_status curast_interpolate(curast_ctx *ctx, uint32_t mesh_id, const float *pos, const float view[16],
+                                 const float proj[16], int W, int H, const uint64_t *vis, const float *attr,
+                                 int C, float *out, curast_stream stream);
+
+/* Backward of curast_interpolate with the visibility held fixed: given
+ * grad_out = dL/dout (device W*H*C), ACCUMULATES dL/dattr into grad_attr
+ * (device V*C, may be NULL) and dL/dpos into grad_pos (device V*3, world
+ * space through the instance's model-view, may be NULL) with FP32 atomics
+ * aggregated per warp.  The caller zeroes the gradients first.  The order of
+ * the atomic additions is not fixed, so results vary in the last bits. */
+curast_status curast_interpolate_backward(curast_ctx *ctx, uint32_t mesh_id, const float *pos,
+                                          const float view[16], const float proj[16], int W, int H,
+                                          const uint64_t *vis, const float *attr, int C, const float *grad_out,
+                                          float *grad_attr, float *grad_pos, curast_stream stream);
+
+/* ------------------------------------------------------- sync & tuning --- */
+
+/* Waits for the stream, then reads the device counters of the last render
+ * into *stats (may be NULL) and returns CURAST_ERR_INDEX_OUT_OF_RANGE if a
+ * device check failed since the previous curast_sync, else CURAST_OK. */
+curast_status curast_sync(curast_ctx *ctx, curast_stream stream, curast_stats *stats);
+
+/* Per-stage device times (ms) of the last render issued on this context:
+ * out[0] clear, [1] stage 1, [2] stage 2, [3] stage 3; waits for them. */
+curast_status curast_stage_times(curast_ctx *ctx, float out[4]);
+
+/* Picks stage thresholds, tile size and batch shape for the given views by
+ * timing candidate configurations with curast_render_batch.  A candidate is
+ * kept only if its visibility buffers equal the default configuration's bit
+ * for bit.  The winner is installed and returned in *chosen (may be NULL).
+ * The views' buffers are overwritten. */
+curast_status curast_autotune(curast_ctx *ctx, const curast_view *views, int n_views, curast_stream stream,
+                              curast_config *chosen);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CURAST_H */

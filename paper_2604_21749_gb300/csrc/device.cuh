@@ -1,0 +1,289 @@
+// device.cuh -- frame tables and the exact per-vertex / per-pixel arithmetic
+// shared by every rasterization stage.
+//
+// All stages cover pixels with one rule (exact integer edge functions on
+// vertices snapped to 1/256 px, sampled at pixel centres, top-left fill
+// rule, y up, CCW front), so which stage handles a triangle never changes the
+// visibility buffer.  Every floating-point operation uses an explicitly
+// rounded intrinsic (__fmul_rn, __fadd_rn, ...) so the compiler cannot fuse
+// or reorder it; the order of operations is the one stated in each comment.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace curast {
+
+constexpr float kGuard = 128.0f;             // clip guard band |x|,|y| <= 128 w
+constexpr float kSnapLimit = 536870912.0f;   // 2^29: bound of snapped coordinates
+constexpr uint64_t kIdMask = (1ull << 36) - 1;
+constexpr uint64_t kEmpty = ~0ull;
+constexpr int kMaxPoly = 9;                  // clipped polygon <= 3 + 5 vertices
+
+// ---------------------------------------------------------------- tables --
+struct ViewDev {             // one view of a frame
+    float fx, fy, nearv;     // projection vector (Eq. 2) and near plane
+    float hw, hh;            // W/2, H/2
+    int32_t W, H;
+    uint64_t *vis;           // W*H visibility words
+};
+
+struct PairDev {             // one (instance, view) pair that survived host culling
+    float mv[12];            // rows 0..2 of view * model, FP32
+    uint64_t base;           // global id of the instance's triangle 0
+    uint32_t view;
+    uint32_t mesh;
+};
+
+struct SegDev {              // a stage-1 work item: one mesh x a run of its pairs
+    uint32_t mesh;
+    uint32_t pair0;
+    uint32_t npairs;
+    uint32_t pad;
+    uint64_t T;              // triangles of the mesh
+    uint64_t batch0;         // first work-grab index of this segment
+};
+
+struct MeshDev {
+    const float *pos;
+    const uint32_t *idx;
+    const uint8_t *rgba;
+    uint64_t V, T;
+};
+
+struct Q1Entry {             // stage 1 -> stage 2: a whole triangle of one pair
+    uint64_t id;
+    uint32_t pair;
+    uint32_t pad;
+};
+
+struct Q2Entry {             // stage 2 -> stage 3: one tile of one sub-triangle
+    int32_t X[3], Y[3];
+    float iz[3];
+    uint32_t view;
+    uint64_t id;
+    uint32_t tx, ty;         // tile coordinates
+};
+
+struct Counters {
+    unsigned long long work;          // stage-1 work grabs
+    unsigned long long q1_count, q1_next;
+    unsigned long long q2_count, q2_next;
+    unsigned long long overflow1, overflow2;
+    unsigned int error, pad;
+    unsigned long long stats[8];      // see Stat
+};
+
+enum Stat { kStatIn = 0, kStatClip, kStatBack, kStatTiny, kStatS1, kStatS2, kStatParts, kStatCount };
+
+// Frame sizes that vary from frame to frame live in device memory, so a
+// launch sequence captured in a CUDA graph stays valid.
+struct FrameHdr {
+    uint64_t n_batches;      // stage-1 work items
+    uint32_t n_segs;
+    uint32_t n_views;
+};
+
+struct FrameDev {
+    const FrameHdr *hdr;
+    const ViewDev *views;
+    const PairDev *pairs;
+    const SegDev *segs;
+    const MeshDev *meshes;
+    Q1Entry *q1;
+    Q2Entry *q2;
+    Counters *ctr;
+    unsigned *err;           // sticky error bits, cleared by curast_sync
+    uint64_t q1_cap, q2_cap;
+    uint32_t s1_max;         // stage-1 bbox pixel limit
+    uint32_t s2_max;         // stage-2 bbox pixel limit
+    uint32_t tile_log2;
+    uint32_t tpt;            // stage-1 triangles per thread per grab
+    uint32_t check;          // bounds-check indices
+    uint32_t stats;          // count statistics
+};
+
+constexpr unsigned kErrIndex = 1u;
+
+// ------------------------------------------------------------ transform --
+struct CV { float x, y, w; };   // clip-space vertex: fx*vx, fy*vy, -vz
+
+// Section 3.1: view-space transform, each row as ((m0 x + m1 y) + m2 z) + m3,
+// then the projection vector of Eq. 2 (x, y scaled by fx, fy; depth = -z).
+__device__ __forceinline__ CV to_clip(const float *mv, float x, float y, float z, float fx, float fy) {
+    float vx = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(mv[0], x), __fmul_rn(mv[1], y)), __fmul_rn(mv[2], z)), mv[3]);
+    float vy = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(mv[4], x), __fmul_rn(mv[5], y)), __fmul_rn(mv[6], z)), mv[7]);
+    float vz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(mv[8], x), __fmul_rn(mv[9], y)), __fmul_rn(mv[10], z)), mv[11]);
+    CV c;
+    c.x = __fmul_rn(fx, vx);
+    c.y = __fmul_rn(fy, vy);
+    c.w = -vz;
+    return c;
+}
+
+// Signed distance-like value of plane p (0 near, 1 left, 2 right, 3 bottom,
+// 4 top of the guard band); the vertex is inside when the value is >= 0.
+__device__ __forceinline__ float plane_value(int p, CV v, float nearv) {
+    const float gw = __fmul_rn(kGuard, v.w);
+    switch (p) {
+    case 0: return __fsub_rn(v.w, nearv);
+    case 1: return __fadd_rn(v.x, gw);
+    case 2: return __fsub_rn(gw, v.x);
+    case 3: return __fadd_rn(v.y, gw);
+    default: return __fsub_rn(gw, v.y);
+    }
+}
+
+// Bit p set when the vertex is outside plane p (NaN counts as outside).
+__device__ __forceinline__ unsigned outcode(CV v, float nearv) {
+    unsigned o = 0;
+#pragma unroll
+    for (int p = 0; p < 5; ++p) o |= (plane_value(p, v, nearv) >= 0.0f) ? 0u : (1u << p);
+    return o;
+}
+
+// Edge from an inside vertex to an outside vertex cut by plane p:
+// t = f_in / (f_in - f_out), r = in + t (out - in); depth of the near-plane
+// point set to near exactly, other points kept at depth >= near.
+__device__ __forceinline__ CV intersect(CV in, CV out, float fin, float fout, int p, float nearv) {
+    float t = __fdiv_rn(fin, __fsub_rn(fin, fout));
+    CV r;
+    r.x = __fadd_rn(in.x, __fmul_rn(t, __fsub_rn(out.x, in.x)));
+    r.y = __fadd_rn(in.y, __fmul_rn(t, __fsub_rn(out.y, in.y)));
+    r.w = __fadd_rn(in.w, __fmul_rn(t, __fsub_rn(out.w, in.w)));
+    if (p == 0) r.w = nearv;
+    else if (r.w < nearv) r.w = nearv;
+    return r;
+}
+
+// Sutherland-Hodgman (Section 3.2) against near, left, right, bottom, top.
+// Returns 0 or the vertex count (3..8); a triangle inside every plane comes
+// back unchanged.
+static __device__ __noinline__ int clip_polygon(const CV tri[3], float nearv, CV out[kMaxPoly]) {
+    CV a[kMaxPoly], b[kMaxPoly];
+    int n = 3;
+    a[0] = tri[0]; a[1] = tri[1]; a[2] = tri[2];
+    for (int p = 0; p < 5 && n > 0; ++p) {
+        int m = 0;
+        CV prev = a[n - 1];
+        float fprev = plane_value(p, prev, nearv);
+        for (int i = 0; i < n; ++i) {
+            CV cur = a[i];
+            float fcur = plane_value(p, cur, nearv);
+            if (fcur >= 0.0f) {
+                if (fprev < 0.0f) b[m++] = intersect(cur, prev, fcur, fprev, p, nearv);
+                b[m++] = cur;
+            } else if (fprev >= 0.0f) {
+                b[m++] = intersect(prev, cur, fprev, fcur, p, nearv);
+            }
+            prev = cur;
+            fprev = fcur;
+        }
+        for (int i = 0; i < m; ++i) a[i] = b[i];
+        n = m;
+    }
+    if (n < 3) return 0;
+    for (int i = 0; i < n; ++i) out[i] = a[i];
+    return n;
+}
+
+// Eq. 2 division by depth, viewport map and snap to 1/256 px:
+// iz = 1/w, s = c * iz, X = (s + 1) * (W/2), Xq = rint(clamp(256 X, +-2^29)).
+__device__ __forceinline__ void snap(CV v, float hw, float hh, int &X, int &Y, float &iz) {
+    float r = __frcp_rn(v.w);
+    float xs = __fmul_rn(__fmul_rn(__fadd_rn(__fmul_rn(v.x, r), 1.0f), hw), 256.0f);
+    float ys = __fmul_rn(__fmul_rn(__fadd_rn(__fmul_rn(v.y, r), 1.0f), hh), 256.0f);
+    xs = fminf(fmaxf(xs, -kSnapLimit), kSnapLimit);
+    ys = fminf(fmaxf(ys, -kSnapLimit), kSnapLimit);
+    X = __float2int_rn(xs);
+    Y = __float2int_rn(ys);
+    iz = r;
+}
+
+// ---------------------------------------------------------------- raster --
+__device__ __forceinline__ int64_t floor_div256(int64_t a) { return a >> 8; }        // arithmetic shift = floor
+__device__ __forceinline__ int64_t ceil_div256(int64_t a) { return -((-a) >> 8); }
+
+// top-left rule, y up, CCW: the edge a->b owns samples on it iff it runs
+// downwards, or horizontally to the left.
+__device__ __forceinline__ bool top_left(int ax, int ay, int bx, int by) {
+    int dx = bx - ax, dy = by - ay;
+    return dy < 0 || (dy == 0 && dx < 0);
+}
+
+// A snapped (sub-)triangle ready for pixel loops.
+struct SubTri {
+    int X[3], Y[3];
+    float iz[3];
+    int64_t A;              // twice the signed area, > 0
+    int x0, x1, y0, y1;     // pixel-centre range clamped to the screen (may be empty)
+    unsigned bias;          // bit k set: edge k is NOT top-left (needs E_k > 0)
+    uint64_t id;
+};
+
+// Sets up a sub-triangle; returns false when it is back-facing, degenerate
+// or covers no pixel centre of the W x H screen.
+__device__ __forceinline__ bool setup_subtri(SubTri &s, int W, int H) {
+    const int64_t A = (int64_t)(s.X[1] - s.X[0]) * (int64_t)(s.Y[2] - s.Y[0]) -
+                      (int64_t)(s.X[2] - s.X[0]) * (int64_t)(s.Y[1] - s.Y[0]);
+    if (A <= 0) return false;
+    s.A = A;
+    int minX = min(s.X[0], min(s.X[1], s.X[2])), maxX = max(s.X[0], max(s.X[1], s.X[2]));
+    int minY = min(s.Y[0], min(s.Y[1], s.Y[2])), maxY = max(s.Y[0], max(s.Y[1], s.Y[2]));
+    int64_t x0 = ceil_div256((int64_t)minX - 128), x1 = floor_div256((int64_t)maxX - 128);
+    int64_t y0 = ceil_div256((int64_t)minY - 128), y1 = floor_div256((int64_t)maxY - 128);
+    x0 = max(x0, (int64_t)0); y0 = max(y0, (int64_t)0);
+    x1 = min(x1, (int64_t)W - 1); y1 = min(y1, (int64_t)H - 1);
+    if (x0 > x1 || y0 > y1) return false;
+    s.x0 = (int)x0; s.x1 = (int)x1; s.y0 = (int)y0; s.y1 = (int)y1;
+    unsigned b = 0;
+    if (!top_left(s.X[1], s.Y[1], s.X[2], s.Y[2])) b |= 1u;
+    if (!top_left(s.X[2], s.Y[2], s.X[0], s.Y[0])) b |= 2u;
+    if (!top_left(s.X[0], s.Y[0], s.X[1], s.Y[1])) b |= 4u;
+    s.bias = b;
+    return true;
+}
+
+// Depth (Section 3.1, perspective-correct): A / sum_k float(E_k) * iz_k, the
+// sum taken as (t0 + t1) + t2; then the 64-bit word depth28 << 36 | id.
+__device__ __forceinline__ uint64_t frag_key(int64_t E0, int64_t E1, int64_t E2, int64_t A, const float iz[3],
+                                             uint64_t id) {
+    float s = __fadd_rn(__fadd_rn(__fmul_rn(__ll2float_rn(E0), iz[0]), __fmul_rn(__ll2float_rn(E1), iz[1])),
+                        __fmul_rn(__ll2float_rn(E2), iz[2]));
+    float depth = __fdiv_rn(__ll2float_rn(A), s);
+    return ((uint64_t)(__float_as_uint(depth) >> 3) << 36) | (id & kIdMask);
+}
+
+// Section 2.1: the closest fragment wins by a 64-bit atomic minimum.  A
+// plain read first skips the atomic when the stored word is already
+// smaller (words only ever decrease, so a stale read is still safe).
+__device__ __forceinline__ void depth_test_write(uint64_t *vis, size_t pix, uint64_t key) {
+    unsigned long long *p = reinterpret_cast<unsigned long long *>(vis + pix);
+    if (key < __ldcg(p)) atomicMin(p, (unsigned long long)key);
+}
+
+// Exact coverage test and write of one pixel (int64 edge functions).
+__device__ __forceinline__ void shade_pixel(const SubTri &s, int x, int y, uint64_t *vis, int W) {
+    const int64_t px = 256 * (int64_t)x + 128, py = 256 * (int64_t)y + 128;
+    const int64_t E0 = (int64_t)(s.X[2] - s.X[1]) * (py - s.Y[1]) - (int64_t)(s.Y[2] - s.Y[1]) * (px - s.X[1]);
+    const int64_t E1 = (int64_t)(s.X[0] - s.X[2]) * (py - s.Y[2]) - (int64_t)(s.Y[0] - s.Y[2]) * (px - s.X[2]);
+    const int64_t E2 = (int64_t)(s.X[1] - s.X[0]) * (py - s.Y[0]) - (int64_t)(s.Y[1] - s.Y[0]) * (px - s.X[0]);
+    const int64_t b0 = s.bias & 1u, b1 = (s.bias >> 1) & 1u, b2 = (s.bias >> 2) & 1u;
+    if (((E0 - b0) | (E1 - b1) | (E2 - b2)) < 0) return;
+    depth_test_write(vis, (size_t)y * (size_t)W + (size_t)x, frag_key(E0, E1, E2, s.A, s.iz, s.id));
+}
+
+// Pixels i = start, start + stride, ... of the sub-triangle's pixel range
+// (x = x0 + i mod w, y = y0 + i / w: the 1D loop of Section 3.2), optionally
+// restricted to a sub-rectangle.
+__device__ __forceinline__ void raster_range(const SubTri &s, int x0, int x1, int y0, int y1, int start, int stride,
+                                             uint64_t *vis, int W) {
+    const int w = x1 - x0 + 1;
+    const int64_t n = (int64_t)w * (int64_t)(y1 - y0 + 1);
+    for (int64_t i = start; i < n; i += stride) {
+        const int y = y0 + (int)(i / w);
+        const int x = x0 + (int)(i - (int64_t)(y - y0) * w);
+        shade_pixel(s, x, y, vis, W);
+    }
+}
+
+}  // namespace curast

@@ -1,0 +1,54 @@
+// internal.h -- launchers the host runtime calls (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace curast {
+
+struct LaunchShape {
+    int stage1_blocks_per_sm[2];   // [single pair, instanced]
+    int stage2_blocks_per_sm;
+    int stage3_blocks_per_sm;
+    int num_sms;
+};
+
+cudaError_t query_launch_shape(LaunchShape *out, int device);
+
+cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s);
+cudaError_t launch_stage1(const FrameDev &f, bool instanced, int blocks, cudaStream_t s);
+cudaError_t launch_stage2(const FrameDev &f, int blocks, cudaStream_t s);
+cudaError_t launch_stage3(const FrameDev &f, int blocks, cudaStream_t s);
+// scratch: 256 * 6 floats; out6: xmin ymin zmin xmax ymax zmax
+cudaError_t launch_aabb(const float *pos, uint64_t V, float *scratch, float *out6, cudaStream_t s);
+cudaError_t launch_count_diff(const uint64_t *a, const uint64_t *b, uint64_t n, unsigned long long *out,
+                              cudaStream_t s);
+
+struct ShadeArgs {
+    const uint64_t *vis;
+    int W, H;
+    float fx, fy;
+    const float *inst_mv;       // n_inst x 12
+    const uint64_t *base;       // n_inst + 1
+    const uint32_t *inst_mesh;  // n_inst
+    const MeshDev *meshes;
+    int n_inst;
+    // resolve
+    float *rgba_f32;
+    uint8_t *rgba8;
+    // interpolate
+    uint32_t mesh;
+    const float *pos;           // overrides the mesh's positions when non-null
+    const float *attr;
+    int C;
+    float *out;
+    const float *grad_out;
+    float *grad_attr;
+    float *grad_pos;
+};
+
+cudaError_t launch_resolve(const ShadeArgs &a, cudaStream_t s);
+cudaError_t launch_interpolate(const ShadeArgs &a, cudaStream_t s);
+cudaError_t launch_interpolate_backward(const ShadeArgs &a, cudaStream_t s);
+
+}  // namespace curast

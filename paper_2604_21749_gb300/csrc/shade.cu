@@ -1,0 +1,241 @@
+// shade.cu -- resolve pass (Section 3.4) and the differentiable interpolation
+// step (forward and backward) on a fixed visibility buffer.
+#include "internal.h"
+
+namespace curast {
+
+// view-space vertex: row r of MV as ((m0 x + m1 y) + m2 z) + m3 (Section 3.1)
+__device__ __forceinline__ float3 view_space(const float *m, const float *p) {
+    float3 v;
+    v.x = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[0], p[0]), __fmul_rn(m[1], p[1])), __fmul_rn(m[2], p[2])), m[3]);
+    v.y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[4], p[0]), __fmul_rn(m[5], p[1])), __fmul_rn(m[6], p[2])), m[7]);
+    v.z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[8], p[0]), __fmul_rn(m[9], p[1])), __fmul_rn(m[10], p[2])), m[11]);
+    return v;
+}
+
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) {
+    return make_float3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)),
+                       __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+                       __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)), __fmul_rn(a.z, b.z));
+}
+
+__device__ __forceinline__ float interp3(float b0, float b1, float b2, float c0, float c1, float c2) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(b0, c0), __fmul_rn(b1, c1)), __fmul_rn(b2, c2));
+}
+
+// Section 3.4: the mesh instance owning a global id is found by binary
+// search of the exclusive prefix sum (last instance with base <= id).
+__device__ __forceinline__ int find_instance(const uint64_t *base, int n, uint64_t id) {
+    int lo = 0, hi = n;   // first index with base[i] > id
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= id) lo = mid + 1; else hi = mid;
+    }
+    return lo - 1;
+}
+
+// Pixel-centre ray through (x, y): (ndx / fx, ndy / fy, -1) with
+// ndx = (2x + 1) / W - 1 (camera at the origin of view space).
+__device__ __forceinline__ float3 pixel_ray(int x, int y, int W, int H, float fx, float fy) {
+    const float ndx = __fsub_rn(__fdiv_rn(__int2float_rn(2 * x + 1), __int2float_rn(W)), 1.0f);
+    const float ndy = __fsub_rn(__fdiv_rn(__int2float_rn(2 * y + 1), __int2float_rn(H)), 1.0f);
+    return make_float3(__fdiv_rn(ndx, fx), __fdiv_rn(ndy, fy), -1.0f);
+}
+
+// Barycentrics of the ray hit with the triangle's plane (Moeller-Trumbore
+// form, unclamped): e1 = v1 - v0, e2 = v2 - v0, p = r x e2, det = e1.p,
+// u = (-v0).p / det, q = (-v0) x e1, w = r.q / det, b = (1 - u - w, u, w).
+__device__ __forceinline__ void ray_bary(float3 r, float3 v0, float3 v1, float3 v2, float &b0, float &b1, float &b2) {
+    const float3 e1 = sub3(v1, v0), e2 = sub3(v2, v0);
+    const float3 tv = make_float3(-v0.x, -v0.y, -v0.z);
+    const float3 pv = cross3(r, e2);
+    const float det = dot3(e1, pv);
+    const float u = __fdiv_rn(dot3(tv, pv), det);
+    const float3 qv = cross3(tv, e1);
+    const float w = __fdiv_rn(dot3(r, qv), det);
+    b0 = __fsub_rn(__fsub_rn(1.0f, u), w);
+    b1 = u;
+    b2 = w;
+}
+
+struct PixelTri {
+    int inst;
+    uint64_t t;
+    uint32_t vi[3];
+    float3 v[3];
+};
+
+__device__ __forceinline__ bool lookup(const ShadeArgs &a, uint64_t key, PixelTri &o, MeshDev &m) {
+    if (key == kEmpty) return false;
+    const uint64_t id = key & kIdMask;
+    const int i = find_instance(a.base, a.n_inst, id);
+    if (i < 0) return false;
+    o.inst = i;
+    o.t = id - a.base[i];
+    m = a.meshes[a.inst_mesh[i]];
+    if (o.t >= m.T) return false;
+    const float *mv = a.inst_mv + 12 * (size_t)i;
+    const float *pos = (a.pos && a.inst_mesh[i] == a.mesh) ? a.pos : m.pos;
+    for (int k = 0; k < 3; ++k) {
+        o.vi[k] = m.idx[3 * o.t + k];
+        o.v[k] = view_space(mv, pos + 3 * (size_t)o.vi[k]);
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- resolve --
+__global__ void __launch_bounds__(256) k_resolve(ShadeArgs a) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= a.W || y >= a.H) return;
+    const size_t pix = (size_t)y * a.W + x;
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    PixelTri pt;
+    MeshDev m;
+    if (lookup(a, a.vis[pix], pt, m) && m.rgba) {
+        float b0, b1, b2;
+        ray_bary(pixel_ray(x, y, a.W, a.H, a.fx, a.fy), pt.v[0], pt.v[1], pt.v[2], b0, b1, b2);
+        const uchar4 q0 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[0]];
+        const uchar4 q1 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[1]];
+        const uchar4 q2 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[2]];
+        const unsigned char s0[4] = {q0.x, q0.y, q0.z, q0.w}, s1[4] = {q1.x, q1.y, q1.z, q1.w},
+                            s2[4] = {q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch)
+            c[ch] = interp3(b0, b1, b2, __fdiv_rn(__uint2float_rn(s0[ch]), 255.0f),
+                            __fdiv_rn(__uint2float_rn(s1[ch]), 255.0f), __fdiv_rn(__uint2float_rn(s2[ch]), 255.0f));
+    }
+    if (a.rgba_f32) reinterpret_cast<float4 *>(a.rgba_f32)[pix] = make_float4(c[0], c[1], c[2], c[3]);
+    if (a.rgba8) {
+        unsigned char q[4];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch)
+            q[ch] = (unsigned char)__float2uint_rn(__fmul_rn(fminf(fmaxf(c[ch], 0.0f), 1.0f), 255.0f));
+        reinterpret_cast<uchar4 *>(a.rgba8)[pix] = make_uchar4(q[0], q[1], q[2], q[3]);
+    }
+}
+
+// ------------------------------------------------------- interpolate fwd --
+__global__ void __launch_bounds__(256) k_interp_fwd(ShadeArgs a) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= a.W || y >= a.H) return;
+    const size_t pix = (size_t)y * a.W + x;
+    PixelTri pt;
+    MeshDev m;
+    float *o = a.out + (size_t)a.C * pix;
+    if (lookup(a, a.vis[pix], pt, m) && a.inst_mesh[pt.inst] == a.mesh) {
+        float b0, b1, b2;
+        ray_bary(pixel_ray(x, y, a.W, a.H, a.fx, a.fy), pt.v[0], pt.v[1], pt.v[2], b0, b1, b2);
+        for (int ch = 0; ch < a.C; ++ch)
+            o[ch] = interp3(b0, b1, b2, a.attr[(size_t)a.C * pt.vi[0] + ch], a.attr[(size_t)a.C * pt.vi[1] + ch],
+                            a.attr[(size_t)a.C * pt.vi[2] + ch]);
+    } else {
+        for (int ch = 0; ch < a.C; ++ch) o[ch] = 0.0f;
+    }
+}
+
+// ------------------------------------------------------- interpolate bwd --
+// Sums `val` over the lanes of the warp holding the same key and adds the
+// sum once per group (warp-aggregated atomics).  All 32 lanes must call it;
+// key 0xFFFFFFFF marks lanes with nothing to add.
+__device__ __forceinline__ void aggregated_add(unsigned key, float *addr, float val) {
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    float sum = val;
+    if (__popc(peers) > 1) {
+        sum = 0.0f;
+        unsigned m = peers;
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            sum += __shfl_sync(peers, val, j);
+        }
+    }
+    if (lane == leader && key != 0xffffffffu) atomicAdd(addr, sum);
+}
+
+constexpr int kMaxC = 16;
+
+// With D_k = r . (v_{k+1} x v_{k+2}) and S = sum_k D_k the barycentrics are
+// b_k = D_k / S, so for g = dL/dI, gamma_k = g . c_k and gbar = sum b_k gamma_k:
+//   dL/dc_k = g b_k,
+//   dL/dv_j = [ (gamma_{j-1} - gbar) (v_{j+1} x r) + (gamma_{j+1} - gbar) (r x v_{j-1}) ] / S,
+//   dL/dp_j = M^T dL/dv_j   (M = the 3x3 part of the instance's model-view).
+__global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    const bool inside = x < a.W && y < a.H;
+    PixelTri pt;
+    MeshDev m;
+    bool hit = false;
+    size_t pix = 0;
+    if (inside) {
+        pix = (size_t)y * a.W + x;
+        hit = lookup(a, a.vis[pix], pt, m) && a.inst_mesh[pt.inst] == a.mesh;
+    }
+    float b[3] = {0.0f, 0.0f, 0.0f};
+    float dv[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+    float g[kMaxC];
+    for (int ch = 0; ch < a.C; ++ch) g[ch] = 0.0f;
+    if (hit) {
+        const float3 r = pixel_ray(x, y, a.W, a.H, a.fx, a.fy);
+        float D[3];
+        for (int k = 0; k < 3; ++k) D[k] = dot3(r, cross3(pt.v[(k + 1) % 3], pt.v[(k + 2) % 3]));
+        const float S = D[0] + D[1] + D[2];
+        const float invS = 1.0f / S;
+        for (int k = 0; k < 3; ++k) b[k] = D[k] * invS;
+        for (int ch = 0; ch < a.C; ++ch) g[ch] = a.grad_out[(size_t)a.C * pix + ch];
+        float gam[3];
+        for (int k = 0; k < 3; ++k) {
+            float s = 0.0f;
+            for (int ch = 0; ch < a.C; ++ch) s += g[ch] * a.attr[(size_t)a.C * pt.vi[k] + ch];
+            gam[k] = s;
+        }
+        const float gbar = b[0] * gam[0] + b[1] * gam[1] + b[2] * gam[2];
+        const float *mv = a.inst_mv + 12 * (size_t)pt.inst;
+        for (int j = 0; j < 3; ++j) {
+            const int jm = (j + 2) % 3, jp = (j + 1) % 3;
+            const float3 c1 = cross3(pt.v[jp], r), c2 = cross3(r, pt.v[jm]);
+            const float w1 = (gam[jm] - gbar) * invS, w2 = (gam[jp] - gbar) * invS;
+            const float3 d = make_float3(w1 * c1.x + w2 * c2.x, w1 * c1.y + w2 * c2.y, w1 * c1.z + w2 * c2.z);
+            // world-space gradient: M^T d
+            for (int ax = 0; ax < 3; ++ax) dv[j][ax] = mv[ax] * d.x + mv[4 + ax] * d.y + mv[8 + ax] * d.z;
+        }
+    }
+    for (int j = 0; j < 3; ++j) {
+        const unsigned key = hit ? pt.vi[j] : 0xffffffffu;
+        if (a.grad_pos)
+            for (int ax = 0; ax < 3; ++ax)
+                aggregated_add(key, a.grad_pos + 3 * (size_t)(hit ? pt.vi[j] : 0) + ax, dv[j][ax]);
+        if (a.grad_attr)
+            for (int ch = 0; ch < a.C; ++ch)
+                aggregated_add(key, a.grad_attr + (size_t)a.C * (hit ? pt.vi[j] : 0) + ch, g[ch] * b[j]);
+    }
+}
+
+// -------------------------------------------------------------- launchers --
+static dim3 pixel_grid(int W, int H) { return dim3((unsigned)((W + 31) / 32), (unsigned)((H + 7) / 8)); }
+
+cudaError_t launch_resolve(const ShadeArgs &a, cudaStream_t s) {
+    k_resolve<<<pixel_grid(a.W, a.H), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate(const ShadeArgs &a, cudaStream_t s) {
+    k_interp_fwd<<<pixel_grid(a.W, a.H), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate_backward(const ShadeArgs &a, cudaStream_t s) {
+    k_interp_bwd<<<pixel_grid(a.W, a.H), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace curast
