@@ -86,8 +86,9 @@ __device__ __forceinline__ bool lookup(const ShadeArgs &a, uint64_t key, PixelTr
     const float *pos = (a.pos && a.inst_mesh[i] == a.mesh) ? a.pos : m.pos;
     for (int k = 0; k < 3; ++k) {
         o.vi[k] = m.idx[3 * o.t + k];
-        o.v[k] = view_space(mv, pos + 3 * (size_t)o.vi[k]);
+        if (o.vi[k] >= m.V) return false;
     }
+    for (int k = 0; k < 3; ++k) o.v[k] = view_space(mv, pos + 3 * (size_t)o.vi[k]);
     return true;
 }
 
@@ -143,15 +144,15 @@ __global__ void __launch_bounds__(256) k_interp_fwd(ShadeArgs a) {
 
 // ------------------------------------------------------- interpolate bwd --
 // Sums `val` over the lanes of the warp holding the same key and adds the
-// sum once per group (warp-aggregated atomics).  All 32 lanes must call it;
-// key 0xFFFFFFFF marks lanes with nothing to add.
-__device__ __forceinline__ void aggregated_add(unsigned key, float *addr, float val) {
+// sum once per group as an FP32 atomicAdd (warp-aggregated atomics).  All
+// 32 lanes must call it; key 0xFFFFFFFF marks lanes with nothing to add.
+__device__ __forceinline__ void aggregated_add(unsigned key, float *addr, double val) {
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(peers) - 1;
-    float sum = val;
+    double sum = val;
     if (__popc(peers) > 1) {
-        sum = 0.0f;
+        sum = 0.0;
         unsigned m = peers;
         while (m) {
             const int j = __ffs(m) - 1;
@@ -159,16 +160,27 @@ __device__ __forceinline__ void aggregated_add(unsigned key, float *addr, float 
             sum += __shfl_sync(peers, val, j);
         }
     }
-    if (lane == leader && key != 0xffffffffu) atomicAdd(addr, sum);
+    if (lane == leader && key != 0xffffffffu) atomicAdd(addr, (float)sum);
 }
 
 constexpr int kMaxC = 16;
 
-// With D_k = r . (v_{k+1} x v_{k+2}) and S = sum_k D_k the barycentrics are
+struct D3 { double x, y, z; };
+__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Gradient of I = sum_k b_k c_k with the visibility held fixed.  With
+// D_k = r . (v_{k+1} x v_{k+2}) and S = sum_k D_k the barycentrics are
 // b_k = D_k / S, so for g = dL/dI, gamma_k = g . c_k and gbar = sum b_k gamma_k:
 //   dL/dc_k = g b_k,
 //   dL/dv_j = [ (gamma_{j-1} - gbar) (v_{j+1} x r) + (gamma_{j+1} - gbar) (r x v_{j-1}) ] / S,
 //   dL/dp_j = M^T dL/dv_j   (M = the 3x3 part of the instance's model-view).
+// A pixel's hit point lies ~100x closer to its triangle's vertices than the
+// vertices lie to the camera, so the per-pixel geometry is evaluated in FP64
+// (from the FP32 positions and model-view); the scatter stays FP32.
 __global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
     const bool inside = x < a.W && y < a.H;
@@ -180,43 +192,55 @@ __global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
         pix = (size_t)y * a.W + x;
         hit = lookup(a, a.vis[pix], pt, m) && a.inst_mesh[pt.inst] == a.mesh;
     }
-    float b[3] = {0.0f, 0.0f, 0.0f};
-    float dv[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
-    float g[kMaxC];
-    for (int ch = 0; ch < a.C; ++ch) g[ch] = 0.0f;
+    double b[3] = {0.0, 0.0, 0.0};
+    double dv[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    double g[kMaxC];
+    for (int ch = 0; ch < a.C; ++ch) g[ch] = 0.0;
     if (hit) {
-        const float3 r = pixel_ray(x, y, a.W, a.H, a.fx, a.fy);
-        float D[3];
-        for (int k = 0; k < 3; ++k) D[k] = dot3(r, cross3(pt.v[(k + 1) % 3], pt.v[(k + 2) % 3]));
-        const float S = D[0] + D[1] + D[2];
-        const float invS = 1.0f / S;
+        const float *mv = a.inst_mv + 12 * (size_t)pt.inst;
+        const float *pos = (a.pos && a.inst_mesh[pt.inst] == a.mesh) ? a.pos : m.pos;
+        D3 v[3];
+        for (int k = 0; k < 3; ++k) {
+            const float *p = pos + 3 * (size_t)pt.vi[k];
+            double c[3];
+            for (int r = 0; r < 3; ++r)
+                c[r] = (double)mv[4 * r] * p[0] + (double)mv[4 * r + 1] * p[1] + (double)mv[4 * r + 2] * p[2] +
+                       (double)mv[4 * r + 3];
+            v[k] = {c[0], c[1], c[2]};
+        }
+        const D3 r = {((2.0 * x + 1.0) / a.W - 1.0) / a.fx, ((2.0 * y + 1.0) / a.H - 1.0) / a.fy, -1.0};
+        const D3 e1 = dsub(v[1], v[0]), e2 = dsub(v[2], v[0]);
+        const double S = ddot(r, dcross(e1, e2));
+        double D[3];
+        D[1] = ddot(r, dcross(e2, v[0]));
+        D[2] = ddot(r, dcross(v[0], e1));
+        D[0] = S - D[1] - D[2];
+        const double invS = 1.0 / S;
         for (int k = 0; k < 3; ++k) b[k] = D[k] * invS;
         for (int ch = 0; ch < a.C; ++ch) g[ch] = a.grad_out[(size_t)a.C * pix + ch];
-        float gam[3];
+        double gam[3];
         for (int k = 0; k < 3; ++k) {
-            float s = 0.0f;
+            double s = 0.0;
             for (int ch = 0; ch < a.C; ++ch) s += g[ch] * a.attr[(size_t)a.C * pt.vi[k] + ch];
             gam[k] = s;
         }
-        const float gbar = b[0] * gam[0] + b[1] * gam[1] + b[2] * gam[2];
-        const float *mv = a.inst_mv + 12 * (size_t)pt.inst;
+        const double gbar = b[0] * gam[0] + b[1] * gam[1] + b[2] * gam[2];
         for (int j = 0; j < 3; ++j) {
             const int jm = (j + 2) % 3, jp = (j + 1) % 3;
-            const float3 c1 = cross3(pt.v[jp], r), c2 = cross3(r, pt.v[jm]);
-            const float w1 = (gam[jm] - gbar) * invS, w2 = (gam[jp] - gbar) * invS;
-            const float3 d = make_float3(w1 * c1.x + w2 * c2.x, w1 * c1.y + w2 * c2.y, w1 * c1.z + w2 * c2.z);
-            // world-space gradient: M^T d
-            for (int ax = 0; ax < 3; ++ax) dv[j][ax] = mv[ax] * d.x + mv[4 + ax] * d.y + mv[8 + ax] * d.z;
+            const D3 c1 = dcross(v[jp], r), c2 = dcross(r, v[jm]);
+            const double w1 = (gam[jm] - gbar) * invS, w2 = (gam[jp] - gbar) * invS;
+            const D3 d = {w1 * c1.x + w2 * c2.x, w1 * c1.y + w2 * c2.y, w1 * c1.z + w2 * c2.z};
+            for (int ax = 0; ax < 3; ++ax)
+                dv[j][ax] = (double)mv[ax] * d.x + (double)mv[4 + ax] * d.y + (double)mv[8 + ax] * d.z;
         }
     }
     for (int j = 0; j < 3; ++j) {
         const unsigned key = hit ? pt.vi[j] : 0xffffffffu;
+        const size_t vj = hit ? pt.vi[j] : 0;
         if (a.grad_pos)
-            for (int ax = 0; ax < 3; ++ax)
-                aggregated_add(key, a.grad_pos + 3 * (size_t)(hit ? pt.vi[j] : 0) + ax, dv[j][ax]);
+            for (int ax = 0; ax < 3; ++ax) aggregated_add(key, a.grad_pos + 3 * vj + ax, dv[j][ax]);
         if (a.grad_attr)
-            for (int ch = 0; ch < a.C; ++ch)
-                aggregated_add(key, a.grad_attr + (size_t)a.C * (hit ? pt.vi[j] : 0) + ch, g[ch] * b[j]);
+            for (int ch = 0; ch < a.C; ++ch) aggregated_add(key, a.grad_attr + (size_t)a.C * vj + ch, g[ch] * b[j]);
     }
 }
 
