@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Frame benchmark of the GB300 visibility-buffer rasterizer.
+
+Default workload: the billion-scale terrain -- 64 seeded heightfield tiles of
+4096 x 4096 cells (2^31 triangles, ~43 GB of FP32 positions, uint32 indices
+and RGBA8 colours resident in HBM) in an 8 x 8 layout, one 3840 x 2160
+overview view whose frustum leaves out 18 tiles.  A step is one frame:
+clear, stage 1, stage 2, stage 3 (curast_render).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank renders its own copy of the
+frame (the rasterizer has no exchange step: replicas only); the time is
+the maximum over ranks and the value counts the triangles of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--tiles", type=int, default=8, help="tiles per side of the terrain")
+    p.add_argument("--cells", type=int, default=4096, help="cells per tile side")
+    p.add_argument("--W", type=int, default=3840)
+    p.add_argument("--H", type=int, default=2160)
+    p.add_argument("--batched", choices=["full", "small", "off"], default="full",
+                   help="also time the batched multi-mesh path against one launch per mesh per view")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--subset", type=int, default=0,
+                   help="profiling aid: give geometry only to this many tiles next to the view centre "
+                        "(same layout, camera and triangle density; the other tiles are empty)")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ ranks ---
+class Ranks:
+    def __init__(self, gpus: int):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if torch.cuda.is_available():
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, "max")
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, "sum")
+
+    def _reduce(self, x, op):
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------- clocks ---
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# -------------------------------------------------------------- workloads ---
+def billion_scene_gpu(tiles: int, cells: int, device, subset: int = 0):
+    import torch
+    import synthetic as S
+    if not subset:
+        return S.scene_billion(device=device, tiles=tiles, n=cells)
+    # tiles nearest the point the overview camera looks at
+    cx, cz = tiles / 2.0, tiles / 2.0
+    order = sorted(range(tiles * tiles), key=lambda k: (k % tiles + 0.5 - cx) ** 2 + (k // tiles + 0.5 - cz) ** 2)
+    sc = S.scene_billion(device=device, tiles=tiles, n=cells, only=order[:subset])
+    for k, m in enumerate(sc.meshes):
+        if m is None:
+            sc.meshes[k] = S.Mesh(pos=torch.zeros((3, 3), device=device),
+                                  idx=torch.zeros((0, 3), dtype=torch.int32, device=device),
+                                  rgba8=torch.zeros((3, 4), dtype=torch.uint8, device=device))
+    return sc
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("raster.cu", "device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2604_21749_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_key: str):
+    """DRAM traffic per stage-1 launch from the committed ncu summary, if it
+    was captured on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = kernel_source_hash()
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == "k_stage1" and f[1] == src and f[2] == workload_key:
+            return float(f[3])
+    return None
+
+
+def cpu_baseline_sample(tiles: int, cells: int, W: int, H: int, frac: float = 1.0):
+    """Times the oracle (single thread) on one tile of the terrain, or on the
+    first `frac` of its triangles; returns (Gtris/s, triangles, seconds)."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    from oracle import oracle as orc
+    k = (tiles // 2) * tiles + tiles // 2       # a central, visible tile
+    sc = S.scene_billion(device="cpu", tiles=tiles, n=cells, only=[k])
+    m = sc.meshes[k]
+    if frac < 1.0:
+        nt = max(1, int(m.T * frac))
+        m.idx = m.idx[:nt].contiguous()
+    counts = [2 * cells * cells] * (tiles * tiles)
+    counts[k] = m.T
+    osc = orc.OracleScene(sc, tri_counts=counts)
+    cam = S.camera_billion(W, H, tiles)
+    vis = np.full((H, W), orc.EMPTY, np.uint64)
+    t0 = time.perf_counter()
+    orc.render(osc, cam, first=k, count=1, out=vis)
+    dt = time.perf_counter() - t0
+    return m.T / dt / 1e9, m.T, dt
+
+
+# ------------------------------------------------------------ our arm ------
+def run_ours(args, ranks: Ranks):
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    import synthetic as S
+    from paper_2604_21749_gb300 import api
+
+    ge.build()
+    dev = torch.device("cuda", ranks.local)
+    torch.cuda.set_device(dev)
+    t_gen = time.perf_counter()
+    sc = billion_scene_gpu(args.tiles, args.cells, dev, args.subset)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    cam = S.camera_billion(args.W, args.H, args.tiles)
+    r = api.Renderer(dev.index)
+    for m in sc.meshes:
+        r.upload_mesh(m.pos, m.idx, m.rgba8)
+    for it in sc.instances:
+        r.add_instance(it.mesh, it.model)
+    vis = r.new_vis(args.W, args.H)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        r.render(cam.view, cam.proj, args.W, args.H, vis)
+        r.sync()
+    info = r.last_frame()
+
+    # timed region: K frames; per-frame stage times come from the events the
+    # library records around each stage on this stream
+    clocks = Clocks(dev.index)
+    ranks.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stage = []
+    for _ in range(args.steps):
+        r.render(cam.view, cam.proj, args.W, args.H, vis)
+        stage.append(r.stage_times())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    ranks.barrier()
+    clk = clocks.stop()
+    ms_frame = ranks.max(ms_total / args.steps)
+    r.sync()
+    # one more frame, untimed, with the per-stage counters on
+    r.set_config(collect_stats=1)
+    r.render(cam.view, cam.proj, args.W, args.H, vis)
+    stats = r.sync()
+    r.set_config(collect_stats=0)
+
+    # end to end through the public API with host buffers: every frame uploads
+    # its tables from pinned host memory inside curast_render, resolves, and
+    # copies the RGBA8 image back into pinned host memory
+    host_img = torch.empty((args.H, args.W, 4), dtype=torch.uint8, pin_memory=True)
+    rgba8 = torch.empty((args.H, args.W, 4), dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        r.render(cam.view, cam.proj, args.W, args.H, vis)
+        r.L.curast_resolve(r._h, api._mat(cam.view), api._mat(cam.proj), args.W, args.H, api._ptr(vis), None,
+                           api._ptr(rgba8), api._stream())
+        host_img.copy_(rgba8, non_blocking=True)
+    torch.cuda.synchronize()
+    ranks.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.render(cam.view, cam.proj, args.W, args.H, vis)
+        r.L.curast_resolve(r._h, api._mat(cam.view), api._mat(cam.proj), args.W, args.H, api._ptr(vis), None,
+                           api._ptr(rgba8), api._stream())
+        host_img.copy_(rgba8, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_ms = ranks.max((time.perf_counter() - t0) * 1e3 / args.steps)
+    h2d = 256 + 40 + info["segments"] * 32 + info["pairs"] * 64 + 12 * 4 * len(sc.instances)
+
+    tris = info["triangles"]
+    total_tris = ranks.sum(tris)
+    gtris = total_tris / (ms_frame * 1e-3) / 1e9
+    s1 = statistics.mean(s[1] for s in stage)
+    s1_bytes = 12.0 * (info["unique_triangles"] + info["unique_vertices"])
+    peak, peak_kind = measured_peaks()
+    achieved = s1_bytes / (s1 * 1e-3) / 1e9
+    workload_key = f"billion{args.tiles}x{args.cells}@{args.W}x{args.H}" + (f"-subset{args.subset}" if args.subset else "")
+    result = {
+        "metric": "frame ms & Gtris/s at 3840x2160 (1B tris), %HBM roofline; batched vs plain",
+        "value": round(gtris, 3),
+        "unit": "Gtris/s",
+        "n_gpus": ranks.world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_frame, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "fp32+int64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"billion-scale terrain: {args.tiles}x{args.tiles} seeded heightfield tiles of "
+                        f"{args.cells}^2 cells ({2 * args.cells ** 2 * args.tiles ** 2} triangles), "
+                        f"{args.W}x{args.H}, overview camera",
+            "triangles_per_frame": tris,
+            "visible_tiles": info["pairs"],
+            "l2": f"inputs larger than L2 ({s1_bytes / 1e9:.1f} GB of indices+positions read per frame)",
+            "parallelism": "replicas" if ranks.world > 1 else "single GPU",
+            "generation_s": round(t_gen, 2),
+        },
+        "stage_ms": {k: round(statistics.mean(s[i] for s in stage), 4)
+                     for i, k in enumerate(["clear", "stage1", "stage2", "stage3"])},
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "k_stage1",
+            "achieved": round(achieved, 1),
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": recorded_traffic(workload_key),
+            "peak_kind": peak_kind,
+            "bytes_per_launch": s1_bytes,
+            "bytes_rule": "12 B per index triple + 12 B per vertex, each mesh read once per launch",
+        },
+        "e2e": {"value": round(total_tris / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gtris/s",
+                "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": args.W * args.H * 4},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+        "frame_stats": {k: v for k, v in stats.items() if v},
+    }
+    r.close()
+    del sc, vis
+    torch.cuda.empty_cache()
+
+    if ranks.rank == 0 and ranks.world == 1 and args.batched != "off":
+        result["batched_vs_plain"] = batched_vs_plain(args, dev)
+    if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
+        g, n, dt = cpu_baseline_sample(args.tiles, args.cells, args.W, args.H)
+        result["cpu_baseline"] = {"value": round(g, 5), "unit": "Gtris/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"one central tile ({n} triangles) of the same frame, "
+                                            f"single-threaded oracle, {dt:.1f} s"}
+    return result
+
+
+def batched_vs_plain(args, dev):
+    """The batched form (one persistent launch over all meshes, instances and
+    views, replayed from a CUDA graph) against one launch sequence per mesh
+    per view, on the many-mesh workload; the buffers must be identical."""
+    import torch
+    import synthetic as S
+    from paper_2604_21749_gb300 import api
+    if args.batched == "full":
+        kw = dict(n_meshes=256, n_instances=10000, tmin=1e4, tmax=2e7)
+        name = "256 meshes (T log-uniform in [1e4, 2e7]), 10000 instances, 2x 3840x2160 + 2x 1920x1080"
+    else:
+        kw = dict(n_meshes=32, n_instances=400, tmin=1e3, tmax=2e5)
+        name = "32 meshes (T log-uniform in [1e3, 2e5]), 400 instances, 2x 3840x2160 + 2x 1920x1080"
+    t0 = time.perf_counter()
+    sc = S.scene_batched(device=dev, **kw)
+    torch.cuda.synchronize()
+    tgen = time.perf_counter() - t0
+    r = api.Renderer(dev.index)
+    for m in sc.meshes:
+        r.upload_mesh(m.pos, m.idx, m.rgba8)
+    for it in sc.instances:
+        r.add_instance(it.mesh, it.model)
+    views = [(c.view, c.proj, c.W, c.H, r.new_vis(c.W, c.H)) for c in sc.cameras]
+    plain_out = [r.new_vis(c.W, c.H) for c in sc.cameras]
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        r.render_batch(views, use_graph=True)
+
+    def plain():
+        for c, vis in zip(sc.cameras, plain_out):
+            r.clear(vis)
+            for m in range(len(sc.meshes)):
+                r.render_mesh(m, c.view, c.proj, c.W, c.H, vis)
+
+    def timeit(fn, reps=2):
+        fn()
+        r.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    tb = timeit(batched)
+    info = r.last_frame()
+    tp = timeit(plain)
+    same = all(torch.equal(v[4], p) for v, p in zip(views, plain_out))
+    r.sync()
+    out = {"workload": name, "batched_ms": round(tb, 3), "plain_ms": round(tp, 3),
+           "speedup": round(tp / tb, 3), "identical": bool(same), "pairs": info["pairs"],
+           "triangle_instance_views": info["triangles"],
+           "batched_gtris_s": round(info["triangles"] / (tb * 1e-3) / 1e9, 2), "generation_s": round(tgen, 1)}
+    r.close()
+    del sc, views, plain_out
+    torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------------ reference arm ------
+def run_reference(args, ranks: Ranks):
+    """The oracle as it stands, on the host cores: each step renders a
+    bounded sample (1/16 of one tile) of the same frame."""
+    frac = 1.0 / 16.0
+    for _ in range(args.warmup):
+        cpu_baseline_sample(args.tiles, args.cells, args.W, args.H, frac)
+    vals, secs, n = [], [], 0
+    for _ in range(args.steps):
+        g, n, dt = cpu_baseline_sample(args.tiles, args.cells, args.W, args.H, frac)
+        vals.append(g)
+        secs.append(dt)
+    v = statistics.mean(vals)
+    total = 2 * args.cells ** 2 * args.tiles ** 2
+    return {
+        "impl": "reference",
+        "metric": "frame ms & Gtris/s at 3840x2160 (1B tris), %HBM roofline; batched vs plain",
+        "value": round(v, 6), "unit": "Gtris/s", "n_gpus": ranks.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(secs), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32+int64", "data": "synthetic",
+        "config": {"workload": f"billion-scale terrain: {args.tiles}x{args.tiles} seeded heightfield tiles of "
+                               f"{args.cells}^2 cells ({total} triangles), {args.W}x{args.H}, overview camera"},
+        "cpu_baseline": {"value": round(v, 6), "unit": "Gtris/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n} triangles (1/16 of one central tile) per step, single-threaded oracle"},
+        "e2e": {"value": round(v, 6), "unit": "Gtris/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        # the oracle runs on rank 0's host cores only; other ranks exit at once
+        if int(os.environ.get("RANK", "0")) == 0:
+            os.environ["WORLD_SIZE"] = "1"
+            print(json.dumps(run_reference(args, Ranks(1))), flush=True)
+        return
+    ranks = Ranks(args.gpus)
+    try:
+        res = run_ours(args, ranks)
+        if ranks.rank == 0:
+            print(json.dumps(res), flush=True)
+    finally:
+        ranks.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -100,6 +100,7 @@ typedef struct {
     uint64_t queued_stage3;      /* tile parts                                          */
     uint64_t queue1_overflow;    /* rasterized in place because queue 1 was full        */
     uint64_t queue2_overflow;
+    uint64_t exact_path;         /* (triangle, pair)s the conservative tiny cull passed on */
     uint32_t device_error;       /* nonzero: an index >= V was found (check_indices)    */
     uint32_t reserved;
 } curast_stats;
@@ -213,6 +214,19 @@ curast_status curast_interpolate_backward(curast_ctx *ctx, uint32_t mesh_id, con
                                           const float view[16], const float proj[16], int W, int H,
                                           const uint64_t *vis, const float *attr, int C, const float *grad_out,
                                           float *grad_attr, float *grad_pos, curast_stream stream);
+
+/* Size of the last frame built by a render call (host-side numbers, valid
+ * as soon as the call returns). */
+typedef struct {
+    uint64_t pairs;              /* (instance, view) pairs left after frustum culling     */
+    uint64_t segments;           /* stage-1 work segments (mesh x run of pairs)           */
+    uint64_t work_items;         /* stage-1 work grabs                                    */
+    uint64_t triangles;          /* sum over pairs of the mesh's triangle count           */
+    uint64_t unique_triangles;   /* sum of T over meshes with at least one pair           */
+    uint64_t unique_vertices;    /* sum of V over the same meshes                         */
+} curast_frame_info;
+
+curast_status curast_last_frame(const curast_ctx *ctx, curast_frame_info *out);
 
 /* ------------------------------------------------------- sync & tuning --- */
 

@@ -26,7 +26,7 @@ EXPORTS = ["curast_create", "curast_destroy", "curast_status_string", "curast_ge
            "curast_upload_mesh", "curast_update_mesh", "curast_add_instance", "curast_clear_instances",
            "curast_clear", "curast_render", "curast_render_mesh", "curast_render_batch", "curast_resolve",
            "curast_interpolate", "curast_interpolate_backward", "curast_sync", "curast_stage_times",
-           "curast_autotune"]
+           "curast_autotune", "curast_last_frame"]
 
 
 class CurastError(RuntimeError):
@@ -55,10 +55,19 @@ class Stats(C.Structure):
     _fields_ = [("triangles_in", C.c_uint64), ("culled_clip", C.c_uint64), ("culled_backface", C.c_uint64),
                 ("culled_tiny", C.c_uint64), ("stage1_rasterized", C.c_uint64), ("queued_stage2", C.c_uint64),
                 ("stage2_rasterized", C.c_uint64), ("queued_stage3", C.c_uint64), ("queue1_overflow", C.c_uint64),
-                ("queue2_overflow", C.c_uint64), ("device_error", C.c_uint32), ("reserved", C.c_uint32)]
+                ("queue2_overflow", C.c_uint64), ("exact_path", C.c_uint64), ("device_error", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class FrameInfo(C.Structure):
+    _fields_ = [("pairs", C.c_uint64), ("segments", C.c_uint64), ("work_items", C.c_uint64),
+                ("triangles", C.c_uint64), ("unique_triangles", C.c_uint64), ("unique_vertices", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _LOCK = threading.Lock()
@@ -97,6 +106,7 @@ def load(build: bool = False, path: Optional[str] = None) -> C.CDLL:
             "curast_interpolate_backward": [vp, u32, vp, fp, fp, i32, i32, vp, vp, i32, vp, vp, vp, vp],
             "curast_sync": [vp, vp, C.POINTER(Stats)],
             "curast_stage_times": [vp, fp],
+            "curast_last_frame": [vp, C.POINTER(FrameInfo)],
             "curast_autotune": [vp, C.POINTER(View), i32, vp, C.POINTER(Config)],
         }
         for name, args in sig.items():
@@ -298,6 +308,11 @@ class Renderer:
         st = Stats()
         _check(self.L.curast_sync(self._h, _stream(stream), C.byref(st)), "curast_sync")
         return st.as_dict()
+
+    def last_frame(self) -> dict:
+        fi = FrameInfo()
+        _check(self.L.curast_last_frame(self._h, C.byref(fi)), "curast_last_frame")
+        return fi.as_dict()
 
     def stage_times(self) -> List[float]:
         out = (C.c_float * 4)()

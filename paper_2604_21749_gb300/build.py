@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 SOURCES = ["raster.cu", "shade.cu", "runtime.cu"]
-HEADERS = ["device.cuh", "internal.h"]
+HEADERS = ["device.cuh", "internal.h", "stage1.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

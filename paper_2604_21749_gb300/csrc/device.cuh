@@ -28,7 +28,14 @@ struct ViewDev {             // one view of a frame
 };
 
 struct PairDev {             // one (instance, view) pair that survived host culling
-    float mv[12];            // rows 0..2 of view * model, FP32
+    float mv[12];            // rows 0..2 of view * model, FP32 (the exact transform)
+    // conservative tiny-triangle cull: rows giving X*w, Y*w (pixels) and w
+    // with FMA, and the bound on how far that estimate and the exact snapped
+    // position can lie apart: margin = ka * max(1/w) + kd pixels, valid
+    // when every w exceeds wsafe; fast = 0 disables the test
+    float fn[12];
+    float ka, kd, wsafe;
+    uint32_t fast;
     uint64_t base;           // global id of the instance's triangle 0
     uint32_t view;
     uint32_t mesh;
@@ -73,7 +80,7 @@ struct Counters {
     unsigned long long stats[8];      // see Stat
 };
 
-enum Stat { kStatIn = 0, kStatClip, kStatBack, kStatTiny, kStatS1, kStatS2, kStatParts, kStatCount };
+enum Stat { kStatIn = 0, kStatClip, kStatBack, kStatTiny, kStatS1, kStatS2, kStatParts, kStatFast, kStatCount };
 
 // Frame sizes that vary from frame to frame live in device memory, so a
 // launch sequence captured in a CUDA graph stays valid.
@@ -102,7 +109,8 @@ struct FrameDev {
     uint32_t stats;          // count statistics
 };
 
-constexpr unsigned kErrIndex = 1u;
+constexpr unsigned kErrIndex = 1u;     // a vertex index >= V was skipped
+constexpr unsigned kErrTimeout = 2u;   // a bounded wait on a bulk copy gave up
 
 // ------------------------------------------------------------ transform --
 struct CV { float x, y, w; };   // clip-space vertex: fx*vx, fy*vy, -vz

@@ -1,6 +1,4 @@
 // raster.cu -- clear, stage 1, stage 2 and stage 3 kernels (Section 3.1-3.3).
-#include <cooperative_groups.h>
-
 #include "internal.h"
 
 namespace curast {
@@ -24,9 +22,9 @@ __global__ void __launch_bounds__(256) k_clear(uint64_t *vis, uint64_t n) {
 
 // ----------------------------------------------------- whole-triangle path --
 // Clips, snaps and fan-rasterizes one triangle with the pixel loop split as
-// (start, stride) -- used by a single thread when a queue is full (stride 1)
-// and by stage 2 (one warp per triangle, stride 32).
-__device__ void raster_triangle_general(const CV c[3], const ViewDev &vw, uint64_t id, int start, int stride) {
+// (start, stride) -- used by a single thread when queue 1 is full.
+__device__ __noinline__ void raster_triangle_general(const CV c[3], const ViewDev &vw, uint64_t id, int start,
+                                                     int stride) {
     CV poly[kMaxPoly];
     const int n = clip_polygon(c, vw.nearv, poly);
     if (n < 3) return;
@@ -48,10 +46,32 @@ __device__ __forceinline__ void stat_add(const FrameDev &f, int k, unsigned long
     if (f.stats && v) atomicAdd(&f.ctr->stats[k], v);
 }
 
+// clip-space vertices of triangle t of a mesh under pair p (from global memory)
+__device__ __forceinline__ void load_clip(const FrameDev &f, const MeshDev &mesh, uint32_t pidx, uint64_t t,
+                                          const ViewDev &vw, CV c[3]) {
+    const float *mv = f.pairs[pidx].mv;
+    for (int k = 0; k < 3; ++k) {
+        const float *q = mesh.pos + 3 * (uint64_t)mesh.idx[3 * t + k];
+        c[k] = to_clip(mv, q[0], q[1], q[2], vw.fx, vw.fy);
+    }
+}
+
+// queue 1 is full: the thread clips and rasterizes its triangle itself.
+// (Out-of-line helpers take structs by value: a reference to the kernel
+// parameter or to a hot-loop local would force that object into local
+// memory for the whole kernel.)
+__device__ __noinline__ void q1_overflow(FrameDev f, uint64_t id, uint32_t pidx, MeshDev mesh, uint64_t t,
+                                         ViewDev vw) {
+    atomicAdd(&f.ctr->overflow1, 1ull);
+    CV c[3];
+    load_clip(f, mesh, pidx, t, vw, c);
+    raster_triangle_general(c, vw, id, 0, 1);
+}
+
 // Warp-aggregated append to queue 1 (ballot + popc + one atomicAdd per warp).
 // Lanes whose slot lies beyond the capacity rasterize their triangle in place.
-__device__ __forceinline__ void q1_append(const FrameDev &f, bool want, uint64_t id, uint32_t pair, const CV c[3],
-                                          const ViewDev &vw) {
+__device__ __forceinline__ void q1_append(const FrameDev &f, bool want, uint64_t id, uint32_t pidx,
+                                          const MeshDev &mesh, uint64_t t, const ViewDev &vw) {
     const unsigned active = __activemask();
     const unsigned m = __ballot_sync(active, want);
     if (m == 0) return;
@@ -65,12 +85,11 @@ __device__ __forceinline__ void q1_append(const FrameDev &f, bool want, uint64_t
     if (slot < f.q1_cap) {
         Q1Entry e;
         e.id = id;
-        e.pair = pair;
+        e.pair = pidx;
         e.pad = 0;
         f.q1[slot] = e;
     } else {
-        atomicAdd(&f.ctr->overflow1, 1ull);
-        raster_triangle_general(c, vw, id, 0, 1);
+        q1_overflow(f, id, pidx, mesh, t, vw);
     }
 }
 
@@ -110,151 +129,58 @@ __device__ __forceinline__ void raster_small(const int X[3], const int Y[3], con
     }
 }
 
+// Per-vertex record of one (instance, view): the snapped screen position and
+// 1/depth, or X = INT_MIN with Y = the clip outcode when the vertex lies
+// outside the near plane or the guard band.
+struct Rec { int X, Y; float iz; };
+constexpr int kOutside = (int)0x80000000;
+
+__device__ __forceinline__ Rec make_rec(CV c, const ViewDev &vw) {
+    Rec r;
+    const unsigned oc = outcode(c, vw.nearv);
+    if (oc) {
+        r.X = kOutside;
+        r.Y = (int)oc;
+        r.iz = 0.0f;
+    } else {
+        snap(c, vw.hw, vw.hh, r.X, r.Y, r.iz);
+    }
+    return r;
+}
+
 enum Class { kDrop = 0, kQueue = 1, kSmall = 2 };
 
-// Transform, clip classification, snap, backface / frustum / tiny culls of
-// one triangle for one (instance, view) pair; returns what to do with it.
-struct Classified {
-    int X[3], Y[3];
-    float iz[3];
-    int64_t A;
-    int x0, x1, y0, y1;
-};
-
-__device__ __forceinline__ int classify(const FrameDev &f, const CV c[3], const ViewDev &vw, Classified &o,
-                                        unsigned &stat_mask) {
-    const unsigned o0 = outcode(c[0], vw.nearv), o1 = outcode(c[1], vw.nearv), o2 = outcode(c[2], vw.nearv);
-    if (o0 & o1 & o2) { stat_mask = 1u << kStatClip; return kDrop; }      // wholly beyond one plane
-    if (o0 | o1 | o2) return kQueue;                                        // crosses near/guard: stage 2 clips
-#pragma unroll
-    for (int k = 0; k < 3; ++k) snap(c[k], vw.hw, vw.hh, o.X[k], o.Y[k], o.iz[k]);
-    const int64_t A = (int64_t)(o.X[1] - o.X[0]) * (int64_t)(o.Y[2] - o.Y[0]) -
-                      (int64_t)(o.X[2] - o.X[0]) * (int64_t)(o.Y[1] - o.Y[0]);
-    if (A <= 0) { stat_mask = 1u << kStatBack; return kDrop; }              // backface or degenerate
-    const int minX = min(o.X[0], min(o.X[1], o.X[2])), maxX = max(o.X[0], max(o.X[1], o.X[2]));
-    const int minY = min(o.Y[0], min(o.Y[1], o.Y[2])), maxY = max(o.Y[0], max(o.Y[1], o.Y[2]));
-    // pixel centres 256 x + 128 inside [min, max], clamped to the screen;
-    // an empty range is the frustum cull and the tiny-triangle cull at once
-    const int x0 = max((int)ceil_div256((int64_t)minX - 128), 0);
-    const int x1 = min((int)floor_div256((int64_t)maxX - 128), vw.W - 1);
-    const int y0 = max((int)ceil_div256((int64_t)minY - 128), 0);
-    const int y1 = min((int)floor_div256((int64_t)maxY - 128), vw.H - 1);
-    if (x0 > x1 || y0 > y1) { stat_mask = 1u << kStatTiny; return kDrop; }
+// Cull tests of one triangle of one (instance, view) from its vertex records:
+// beyond one clip plane -> drop; crossing the near plane or the guard band
+// -> stage 2 (clipping); back-facing or degenerate -> drop; bbox without a
+// pixel centre on screen (frustum and tiny-triangle cull) -> drop; bbox over
+// the stage-1 limit -> stage 2; else rasterize here.
+__device__ __forceinline__ int classify(const FrameDev &f, const Rec r[3], const ViewDev &vw, int &x0, int &x1,
+                                        int &y0, int &y1, int64_t &A, unsigned &stat) {
+    if (r[0].X == kOutside || r[1].X == kOutside || r[2].X == kOutside) {
+        const unsigned o0 = r[0].X == kOutside ? (unsigned)r[0].Y : 0u;
+        const unsigned o1 = r[1].X == kOutside ? (unsigned)r[1].Y : 0u;
+        const unsigned o2 = r[2].X == kOutside ? (unsigned)r[2].Y : 0u;
+        if (o0 & o1 & o2) { stat = kStatClip; return kDrop; }
+        return kQueue;
+    }
+    A = (int64_t)(r[1].X - r[0].X) * (int64_t)(r[2].Y - r[0].Y) - (int64_t)(r[2].X - r[0].X) * (int64_t)(r[1].Y - r[0].Y);
+    if (A <= 0) { stat = kStatBack; return kDrop; }
+    const int minX = min(r[0].X, min(r[1].X, r[2].X)), maxX = max(r[0].X, max(r[1].X, r[2].X));
+    const int minY = min(r[0].Y, min(r[1].Y, r[2].Y)), maxY = max(r[0].Y, max(r[1].Y, r[2].Y));
+    // pixel centres 256 x + 128 inside [min, max] (arithmetic shifts are
+    // floor divisions), clamped to the screen
+    x0 = max(-((128 - minX) >> 8), 0);
+    x1 = min((maxX - 128) >> 8, vw.W - 1);
+    y0 = max(-((128 - minY) >> 8), 0);
+    y1 = min((maxY - 128) >> 8, vw.H - 1);
+    if (x0 > x1 || y0 > y1) { stat = kStatTiny; return kDrop; }
     if (maxX - minX >= (1 << 14) || maxY - minY >= (1 << 14)) return kQueue;
     if ((uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1)) > f.s1_max) return kQueue;
-    o.A = A;
-    o.x0 = x0; o.x1 = x1; o.y0 = y0; o.y1 = y1;
     return kSmall;
 }
 
-// Persistent stage-1 kernel (Section 3.1 "Looping Through Batches"): a
-// fixed set of blocks grabs work items from a global counter until none are
-// left.  A work item is blockDim * tpt consecutive triangles of one segment
-// (a mesh and a run of its (instance, view) pairs); each thread loads its
-// triangle's indices and positions once and rasterizes it for every pair of
-// the segment (Section 3.5, extended to several views).  The next grab is
-// issued one item ahead so its latency hides behind the current item.
-template <bool INSTANCED>
-__global__ void __launch_bounds__(256) k_stage1(FrameDev f) {
-    __shared__ unsigned long long s_b;
-    __shared__ SegDev s_seg;
-    const unsigned tid = threadIdx.x;
-    unsigned long long pre = 0;
-    int segidx = 0;
-    const uint64_t n_batches = f.hdr->n_batches;
-    const int n_segs = (int)f.hdr->n_segs;
-    auto find_segment = [&](unsigned long long b) {
-        // batches only grow for one block, so search forward (galloping)
-        int lo = segidx, step = 1, hi;
-        while (true) {
-            hi = lo + step;
-            if (hi >= n_segs || f.segs[hi].batch0 > b) break;
-            lo = hi;
-            step <<= 1;
-        }
-        if (hi > n_segs) hi = n_segs;
-        while (hi - lo > 1) {              // invariant: batch0[lo] <= b < batch0[hi]
-            const int mid = (lo + hi) >> 1;
-            if (f.segs[mid].batch0 <= b) lo = mid; else hi = mid;
-        }
-        segidx = lo;
-        s_seg = f.segs[lo];
-    };
-    if (tid == 0) {
-        const unsigned long long b = atomicAdd(&f.ctr->work, 1ull);
-        s_b = b;
-        if (b < n_batches) find_segment(b);
-        pre = atomicAdd(&f.ctr->work, 1ull);
-    }
-    __syncthreads();
-    const uint64_t per_item = (uint64_t)blockDim.x * f.tpt;
-    for (;;) {
-        const unsigned long long b = s_b;
-        if (b >= n_batches) break;
-        const SegDev seg = s_seg;
-        const MeshDev mesh = f.meshes[seg.mesh];
-        const uint64_t t0 = (b - seg.batch0) * per_item;
-        unsigned long long n_in = 0, n_clip = 0, n_back = 0, n_tiny = 0, n_s1 = 0;
-        for (uint32_t k = 0; k < f.tpt; ++k) {
-            const uint64_t t = t0 + (uint64_t)k * blockDim.x + tid;
-            if (t >= seg.T) break;
-            const uint32_t *ip = mesh.idx + 3 * t;
-            const uint32_t i0 = __ldg(ip), i1 = __ldg(ip + 1), i2 = __ldg(ip + 2);
-            if (f.check && (i0 >= mesh.V || i1 >= mesh.V || i2 >= mesh.V)) {
-                atomicOr(f.err, kErrIndex);
-                continue;
-            }
-            const float *q0 = mesh.pos + 3 * (uint64_t)i0, *q1 = mesh.pos + 3 * (uint64_t)i1,
-                        *q2 = mesh.pos + 3 * (uint64_t)i2;
-            const float x0 = __ldg(q0), y0 = __ldg(q0 + 1), z0 = __ldg(q0 + 2);
-            const float x1 = __ldg(q1), y1 = __ldg(q1 + 1), z1 = __ldg(q1 + 2);
-            const float x2 = __ldg(q2), y2 = __ldg(q2 + 1), z2 = __ldg(q2 + 2);
-            const uint32_t np = INSTANCED ? seg.npairs : 1u;
-            for (uint32_t pi = 0; pi < np; ++pi) {
-                const uint32_t pidx = seg.pair0 + pi;
-                const PairDev &pr = f.pairs[pidx];
-                const ViewDev &vw = f.views[pr.view];
-                float mv[12];
-#pragma unroll
-                for (int j = 0; j < 12; ++j) mv[j] = pr.mv[j];
-                const float fx = vw.fx, fy = vw.fy;
-                CV c[3];
-                c[0] = to_clip(mv, x0, y0, z0, fx, fy);
-                c[1] = to_clip(mv, x1, y1, z1, fx, fy);
-                c[2] = to_clip(mv, x2, y2, z2, fx, fy);
-                Classified o;
-                unsigned sm = 0;
-                const int cls = classify(f, c, vw, o, sm);
-                const uint64_t id = pr.base + t;
-                q1_append(f, cls == kQueue, id, pidx, c, vw);
-                if (cls == kSmall) raster_small(o.X, o.Y, o.iz, o.A, o.x0, o.x1, o.y0, o.y1, id, vw.vis, vw.W);
-                if (f.stats) {
-                    n_in += 1;
-                    n_clip += (sm >> kStatClip) & 1u;
-                    n_back += (sm >> kStatBack) & 1u;
-                    n_tiny += (sm >> kStatTiny) & 1u;
-                    n_s1 += cls == kSmall;
-                }
-            }
-        }
-        if (f.stats) {
-            stat_add(f, kStatIn, n_in);
-            stat_add(f, kStatClip, n_clip);
-            stat_add(f, kStatBack, n_back);
-            stat_add(f, kStatTiny, n_tiny);
-            stat_add(f, kStatS1, n_s1);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            s_b = pre;
-            if (pre < n_batches) {
-                find_segment(pre);
-                pre = atomicAdd(&f.ctr->work, 1ull);
-            }
-        }
-        __syncthreads();
-    }
-}
+#include "stage1.cuh"
 
 // ---------------------------------------------------------------- stage 2 --
 // Section 3.2: one warp per queued triangle.  The triangle is clipped
@@ -304,15 +230,8 @@ __global__ void __launch_bounds__(256) k_stage2(FrameDev f) {
         const PairDev &pr = f.pairs[e.pair];
         const ViewDev vw = f.views[pr.view];
         const MeshDev mesh = f.meshes[pr.mesh];
-        const uint64_t t = e.id - pr.base;
-        float mv[12];
-        for (int j = 0; j < 12; ++j) mv[j] = pr.mv[j];
         CV c[3];
-        for (int k = 0; k < 3; ++k) {
-            const uint32_t vi = mesh.idx[3 * t + k];
-            const float *q = mesh.pos + 3 * (uint64_t)vi;
-            c[k] = to_clip(mv, q[0], q[1], q[2], vw.fx, vw.fy);
-        }
+        load_clip(f, mesh, e.pair, e.id - pr.base, vw, c);
         CV poly[kMaxPoly];
         const int np = clip_polygon(c, vw.nearv, poly);
         if (np < 3) continue;
@@ -422,19 +341,18 @@ __global__ void k_aabb_final(const float *part, int n, float *out) {
     out[k] = v;
 }
 
-cudaError_t launch_aabb(const float *pos, uint64_t V, float *scratch, float *out6, cudaStream_t s) {
-    k_aabb_partial<<<kAabbBlocks, 256, 0, s>>>(pos, V, scratch);
-    k_aabb_final<<<1, 32, 0, s>>>(scratch, kAabbBlocks, out6);
-    return cudaGetLastError();
-}
-
 // -------------------------------------------------------------- launchers --
 cudaError_t query_launch_shape(LaunchShape *o, int device) {
     cudaError_t e = cudaDeviceGetAttribute(&o->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1_blocks_per_sm[0], k_stage1<false>, 256, 0);
+    const size_t sm0 = stage1_smem_bytes<false>(), sm1 = stage1_smem_bytes<true>();
+    e = cudaFuncSetAttribute(k_stage1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1_blocks_per_sm[1], k_stage1<true>, 256, 0);
+    e = cudaFuncSetAttribute(k_stage1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1_blocks_per_sm[0], k_stage1<false>, s1::kThreads, sm0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1_blocks_per_sm[1], k_stage1<true>, s1::kThreads, sm1);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage2_blocks_per_sm, k_stage2, 256, 0);
     if (e != cudaSuccess) return e;
@@ -452,8 +370,8 @@ cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s) {
 }
 
 cudaError_t launch_stage1(const FrameDev &f, bool instanced, int blocks, cudaStream_t s) {
-    if (instanced) k_stage1<true><<<blocks, 256, 0, s>>>(f);
-    else k_stage1<false><<<blocks, 256, 0, s>>>(f);
+    if (instanced) k_stage1<true><<<blocks, s1::kThreads, stage1_smem_bytes<true>(), s>>>(f);
+    else k_stage1<false><<<blocks, s1::kThreads, stage1_smem_bytes<false>(), s>>>(f);
     return cudaGetLastError();
 }
 
@@ -464,6 +382,12 @@ cudaError_t launch_stage2(const FrameDev &f, int blocks, cudaStream_t s) {
 
 cudaError_t launch_stage3(const FrameDev &f, int blocks, cudaStream_t s) {
     k_stage3<<<blocks, 256, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aabb(const float *pos, uint64_t V, float *scratch, float *out6, cudaStream_t s) {
+    k_aabb_partial<<<kAabbBlocks, 256, 0, s>>>(pos, V, scratch);
+    k_aabb_final<<<1, 32, 0, s>>>(scratch, kAabbBlocks, out6);
     return cudaGetLastError();
 }
 

@@ -136,6 +136,45 @@ bool instance_visible(const float *mv, const MeshRec &m, const Cam &cam) {
     return !(all_near || all_l || all_r || all_b || all_t);
 }
 
+// Constants of the conservative tiny-triangle cull of one (instance, view).
+// The fast estimate X_f = (fn_x . p) / (fn_w . p) uses FMA and an
+// approximate reciprocal; the exact path is the FP32 sequence of the
+// projection (Eq. 2) and the snap.  With S_r = sum_j |m_rj a_j| + |m_r3|
+// (a_j the largest |coordinate| of the mesh bounds) and |s| <= 4, forward
+// error analysis (u = 2^-24, reciprocal error taken as 2^-20) gives
+//   |X_f - X_exact| <= hw u (9 fx S_0 + 40 S_2) / w + hw (5 2^-20 + 25 u) + 1/512,
+// which ka / w + kd below exceeds by a wide factor.  wsafe keeps the exact
+// depth of every vertex above the near plane.
+void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
+    std::memset(p.fn, 0, sizeof(p.fn));
+    p.ka = p.kd = p.wsafe = 0.0f;
+    p.fast = 0;
+    if (!m.bounded) return;
+    const double u = std::ldexp(1.0, -24), er = std::ldexp(1.0, -20);
+    double amax[3], S[3];
+    for (int j = 0; j < 3; ++j) amax[j] = std::max(std::fabs(m.lo[j]), std::fabs(m.hi[j]));
+    for (int r = 0; r < 3; ++r) {
+        S[r] = std::fabs((double)p.mv[4 * r + 3]);
+        for (int j = 0; j < 3; ++j) S[r] += std::fabs((double)p.mv[4 * r + j]) * amax[j];
+    }
+    const double hw = v.hw, hh = v.hh, fx = v.fx, fy = v.fy;
+    for (int j = 0; j < 4; ++j) {
+        const double wr = -(double)p.mv[8 + j];
+        p.fn[j] = (float)(hw * (fx * (double)p.mv[j] + wr));
+        p.fn[4 + j] = (float)(hh * (fy * (double)p.mv[4 + j] + wr));
+        p.fn[8 + j] = (float)wr;
+    }
+    const double ka = 1.01 * u * std::max(hw * (16 * fx * S[0] + 64 * S[2]), hh * (16 * fy * S[1] + 64 * S[2]));
+    const double kd = std::max(hw, hh) * (8 * er + 64 * u) + 1.0 / 256 + 1.0 / 512;
+    const double ws = v.nearv * (1 + 1e-3) + 8 * u * S[2];
+    if (!std::isfinite(ka) || !std::isfinite(kd) || !std::isfinite(ws) || ka > 1e30 || ws > 1e30) return;
+    // round the constants up so the float copies stay conservative
+    p.ka = (float)(ka * (1 + 1e-6));
+    p.kd = (float)(kd * (1 + 1e-6));
+    p.wsafe = (float)(ws * (1 + 1e-6));
+    p.fast = 1;
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 curast_config default_config() {
@@ -144,7 +183,7 @@ curast_config default_config() {
     c.stage1_max_pixels = 128;
     c.stage2_max_pixels = 4096;
     c.tile_log2 = 6;
-    c.stage1_tri_per_thread = 8;
+    c.stage1_tri_per_thread = 4;
     c.pairs_per_segment = 64;
     c.queue1_capacity = 1ull << 22;
     c.queue2_capacity = 1ull << 21;
@@ -308,6 +347,7 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
                 p.base = c->base[i];
                 p.view = (uint32_t)v;
                 p.mesh = (uint32_t)m;
+                fast_constants(p, mr, c->hv[v]);
                 c->hp.push_back(p);
             }
         }
@@ -521,8 +561,8 @@ curast_status compute_bounds(curast_ctx *c, MeshRec &m) {
 
 bool valid_config(const curast_config &c) {
     return c.stage1_max_pixels >= 1 && c.stage1_max_pixels <= 1024 && c.stage2_max_pixels >= 32 &&
-           c.tile_log2 >= 4 && c.tile_log2 <= 7 && c.stage1_tri_per_thread >= 1 && c.stage1_tri_per_thread <= 32 &&
-           c.pairs_per_segment >= 1 && c.pairs_per_segment <= 65536 && c.queue1_capacity >= 1 &&
+           c.tile_log2 >= 4 && c.tile_log2 <= 7 && c.stage1_tri_per_thread >= 1 && c.stage1_tri_per_thread <= 4 &&
+           c.pairs_per_segment >= 1 && c.pairs_per_segment <= 64 && c.queue1_capacity >= 1 &&
            c.queue2_capacity >= 1 && c.queue1_capacity <= (1ull << 32) && c.queue2_capacity <= (1ull << 32);
 }
 
@@ -799,9 +839,29 @@ curast_status curast_sync(curast_ctx *c, curast_stream stream, curast_stats *sta
         stats->queued_stage3 = h.q2_count;
         stats->queue1_overflow = h.overflow1;
         stats->queue2_overflow = h.overflow2;
+        stats->exact_path = h.stats[kStatFast];
         stats->device_error = err;
     }
+    if (err & kErrTimeout) return CURAST_ERR_DEVICE_TIMEOUT;
     return (err & kErrIndex) ? CURAST_ERR_INDEX_OUT_OF_RANGE : CURAST_OK;
+}
+
+curast_status curast_last_frame(const curast_ctx *c, curast_frame_info *out) {
+    if (!c || !out) return CURAST_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->pairs = c->hp.size();
+    out->segments = c->hs.size();
+    out->work_items = c->hdr.n_batches;
+    std::vector<char> seen(c->meshes.size(), 0);
+    for (const PairDev &p : c->hp) {
+        out->triangles += c->meshes[p.mesh].T;
+        if (!seen[p.mesh]) {
+            seen[p.mesh] = 1;
+            out->unique_triangles += c->meshes[p.mesh].T;
+            out->unique_vertices += c->meshes[p.mesh].V;
+        }
+    }
+    return CURAST_OK;
 }
 
 curast_status curast_stage_times(curast_ctx *c, float out[4]) {
@@ -867,12 +927,12 @@ curast_status curast_autotune(curast_ctx *c, const curast_view *views, int n_vie
     bool exact = true;
     if (st == CURAST_OK) st = measure(base, &best_ms, &exact);
     // coordinate descent over the batch shape, the two stage thresholds and the tile size
-    const uint32_t tpts[] = {2, 4, 8, 16};
+    const uint32_t tpts[] = {1, 2, 4};
     const uint32_t s1s[] = {32, 64, 128, 256};
     const uint32_t s2s[] = {1024, 4096, 16384};
     const uint32_t tiles[] = {5, 6, 7};
     for (int dim = 0; dim < 4 && st == CURAST_OK; ++dim) {
-        const int n = dim == 0 ? 4 : dim == 1 ? 4 : dim == 2 ? 3 : 3;
+        const int n = dim == 0 ? 3 : dim == 1 ? 4 : dim == 2 ? 3 : 3;
         for (int k = 0; k < n && st == CURAST_OK; ++k) {
             curast_config cand = best;
             if (dim == 0) cand.stage1_tri_per_thread = tpts[k];

@@ -1,0 +1,389 @@
+// stage1.cuh -- the persistent stage-1 kernel (Section 3.1), included by raster.cu.
+//
+// Warp-specialized pipeline: one producer warp grabs work items from the
+// global counter, stages each item's index triples in shared memory with a
+// TMA bulk copy and fills the item's per-(instance, view) constants; eight
+// consumer warps cull and rasterize.  Producer and consumers meet only at
+// full / empty mbarriers of a three-slot ring, so no block-wide barrier
+// stalls the consumers.
+#pragma once
+
+// ------------------------------------------------------- TMA / mbarrier --
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1D bulk copy global -> shared (TMA engine), completion counted in bytes
+// on the mbarrier.  dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a phase of an mbarrier; false after 2^24 polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 24); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// --------------------------------------------- conservative tiny cull --
+// Per (instance, view) constants of the fast test, staged in shared memory:
+// rows giving X*w, Y*w (pixels) and w by FMA, the error bound
+// margin = ka * max(1/w) + kd, the depth wsafe every vertex must exceed and
+// the window of +-4 screen widths the test is valid in.
+struct __align__(16) FastPair {
+    float4 rx, ry, rw;          // (fn[4r], fn[4r+1], fn[4r+2], fn[4r+3])
+    float4 k;                   // ka, kd, wsafe, fast (0 or 1)
+    float4 lim;                 // xlo, xhi, ylo, yhi
+    float wmax, hmax;           // last pixel centre W - 1/2, H - 1/2
+    int pad0, pad1;
+};
+
+struct Tri9 { float v[9]; };    // the three vertices of a triangle, passed by value
+
+// The "bbox holds no pixel centre" test of Section 3.1, done before the
+// exact arithmetic: the estimated bbox widened by the error bound must hold
+// no pixel centre of the screen while every vertex lies safely in front of
+// the near plane and inside the window -- then the exact snapped bbox holds
+// none either and the exact path would drop the triangle as well.
+// Evaluated without branches.
+__device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
+    // vertex by vertex into running bounds (few live registers)
+    float xmn = INFINITY, xmx = -INFINITY, ymn = INFINITY, ymx = -INFINITY, wmn = INFINITY, rmx = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float x = p.v[3 * c], y = p.v[3 * c + 1], z = p.v[3 * c + 2];
+        const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw;
+        const float xw = __fmaf_rn(rx.x, x, __fmaf_rn(rx.y, y, __fmaf_rn(rx.z, z, rx.w)));
+        const float yw = __fmaf_rn(ry.x, x, __fmaf_rn(ry.y, y, __fmaf_rn(ry.z, z, ry.w)));
+        const float w = __fmaf_rn(rw.x, x, __fmaf_rn(rw.y, y, __fmaf_rn(rw.z, z, rw.w)));
+        const float r = rcp_approx(w);
+        const float X = xw * r, Y = yw * r;
+        xmn = fminf(xmn, X); xmx = fmaxf(xmx, X);
+        ymn = fminf(ymn, Y); ymx = fmaxf(ymx, Y);
+        wmn = fminf(wmn, w); rmx = fmaxf(rmx, r);
+    }
+    const float4 k = fp.k, lim = fp.lim;
+    const float m = __fmaf_rn(k.x, rmx, k.y);
+    const float xl = xmn - m, xh = xmx + m, yl = ymn - m, yh = ymx + m;
+    const bool safe = (wmn > k.z) & (xl > lim.x) & (xh < lim.y) & (yl > lim.z) & (yh < lim.w) & (k.w != 0.0f);
+    // no pixel centre i + 1/2 (0 <= i < W) in [lo, hi]: floor(hi - 1/2) < lo - 1/2,
+    // or the interval ends before the first centre / starts after the last
+    // (exact subtractions: inside the window |lo|, |hi| < 2^22)
+    const bool nx = (floorf(xh - 0.5f) < xl - 0.5f) | (xh < 0.5f) | (xl > fp.wmax);
+    const bool ny = (floorf(yh - 0.5f) < yl - 0.5f) | (yh < 0.5f) | (yl > fp.hmax);
+    return safe & (nx | ny);
+}
+
+// The exact path of one triangle for one (instance, view): FP32 transform in
+// the fixed order, clip outcodes, snap, culls, then stage-1 raster or queue 1.
+__device__ __noinline__ void exact_triangle(FrameDev f, MeshDev mesh, uint32_t pidx, uint64_t t, Tri9 p,
+                                            bool live) {
+    const PairDev &pr = f.pairs[pidx];
+    const ViewDev vw = f.views[pr.view];
+    Rec r[3];
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    int64_t A = 0;
+    unsigned st = kStatCount;
+    int cls = kDrop;
+    if (live) {
+        float mv[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) mv[q] = pr.mv[q];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            r[k] = make_rec(to_clip(mv, p.v[3 * k], p.v[3 * k + 1], p.v[3 * k + 2], vw.fx, vw.fy), vw);
+        cls = classify(f, r, vw, x0, x1, y0, y1, A, st);
+    }
+    const uint64_t id = pr.base + t;
+    q1_append(f, cls == kQueue, id, pidx, mesh, t, vw);
+    if (cls == kSmall) {
+        const int X[3] = {r[0].X, r[1].X, r[2].X}, Y[3] = {r[0].Y, r[1].Y, r[2].Y};
+        const float iz[3] = {r[0].iz, r[1].iz, r[2].iz};
+        raster_small(X, Y, iz, A, x0, x1, y0, y1, id, vw.vis, vw.W);
+    }
+    if (f.stats && live) {
+        stat_add(f, kStatIn, 1);
+        if (st != kStatCount) stat_add(f, st, 1);
+        if (cls == kSmall) stat_add(f, kStatS1, 1);
+    }
+}
+
+// ----------------------------------------------------------- the kernel --
+namespace s1 {
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = 32 * kConsumerWarps;      // 256 consumer threads
+constexpr int kThreads = kConsumers + 32;            // + one producer warp
+constexpr int kMaxTpt = 4;                           // triangles per consumer per item
+constexpr int kItem = kConsumers * kMaxTpt;          // 1024 triangles, 12 KB of index triples
+constexpr int kSlots = 3;
+constexpr int kQueue = 64;                           // per-warp survivors of the fast cull
+constexpr int kMaxPairs = 64;                        // pairs of one segment (pairs_per_segment <= 64)
+
+struct Desc {
+    unsigned long long b;  // work item, >= n_batches: none (consumers stop)
+    uint64_t t0;           // first triangle of the item within its mesh
+    uint32_t n;            // triangles in the item
+    uint32_t mesh, pair0, npairs;
+};
+
+template <bool INST>
+struct Smem {
+    uint32_t idx[kSlots][3 * kItem];
+    FastPair fp[kSlots][INST ? kMaxPairs : 1];
+    MeshDev mesh[kSlots];
+    Desc desc[kSlots];
+    uint64_t full[kSlots], empty[kSlots];
+    uint4 wq[kConsumerWarps][kQueue];                // (triangle lo, hi, pair, mesh)
+};
+}  // namespace s1
+
+template <bool INST>
+size_t stage1_smem_bytes() { return sizeof(s1::Smem<INST>); }
+
+// Producer warp: work grabs (Section 3.1 "Looping Through Batches": a
+// global counter hands out items until all triangles are done; the counter
+// is read one grab ahead), the forward search for the item's segment, the
+// item's pair constants, and the TMA copy of its index triples.
+template <bool INST>
+__device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST> &S, uint64_t n_batches,
+                                                int n_segs, uint64_t per_item) {
+    using namespace s1;
+    const int lane = threadIdx.x & 31;
+    unsigned long long next = 0;
+    int segidx = 0;
+    unsigned long long seg_end = 0;
+    SegDev seg{};
+    bool have = false;
+    if (lane == 0) next = atomicAdd(&f.ctr->work, 1ull);
+    for (int j = 0;; ++j) {
+        const int slot = j % kSlots;
+        if (j >= kSlots && !mbar_wait(&S.empty[slot], ((j / kSlots) - 1) & 1u)) {
+            if (lane == 0) atomicOr(f.err, kErrTimeout);
+            return;
+        }
+        Desc d{};
+        if (lane == 0) {
+            const unsigned long long b = next;
+            d.b = b;
+            if (b < n_batches) {
+                next = atomicAdd(&f.ctr->work, 1ull);
+                if (!have || b >= seg_end) {          // galloping forward search: grabs only grow
+                    int lo = segidx, step = 1, hi;
+                    while (true) {
+                        hi = lo + step;
+                        if (hi >= n_segs || f.segs[hi].batch0 > b) break;
+                        lo = hi;
+                        step <<= 1;
+                    }
+                    if (hi > n_segs) hi = n_segs;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (f.segs[mid].batch0 <= b) lo = mid; else hi = mid;
+                    }
+                    segidx = lo;
+                    seg = f.segs[lo];
+                    seg_end = lo + 1 < n_segs ? f.segs[lo + 1].batch0 : ~0ull;
+                    have = true;
+                }
+                d.t0 = (b - seg.batch0) * per_item;
+                const uint64_t left = seg.T - d.t0;
+                d.n = (uint32_t)(left < per_item ? left : per_item);
+                d.mesh = seg.mesh;
+                d.pair0 = seg.pair0;
+                d.npairs = INST ? seg.npairs : 1u;
+            }
+            S.desc[slot] = d;
+        }
+        d.b = __shfl_sync(0xffffffffu, d.b, 0);
+        if (d.b >= n_batches) {                       // tell the consumers to stop
+            __syncwarp();
+            mbar_arrive(&S.full[slot]);
+            return;
+        }
+        d.t0 = __shfl_sync(0xffffffffu, d.t0, 0);
+        d.n = __shfl_sync(0xffffffffu, d.n, 0);
+        d.mesh = __shfl_sync(0xffffffffu, d.mesh, 0);
+        d.pair0 = __shfl_sync(0xffffffffu, d.pair0, 0);
+        d.npairs = __shfl_sync(0xffffffffu, d.npairs, 0);
+        const MeshDev &mesh = f.meshes[d.mesh];
+        if (lane == 0) S.mesh[slot] = mesh;
+        for (uint32_t q = lane; q < d.npairs; q += 32) {
+            const PairDev &pr = f.pairs[d.pair0 + q];
+            const ViewDev &vw = f.views[pr.view];
+            FastPair fp;
+            fp.rx = make_float4(pr.fn[0], pr.fn[1], pr.fn[2], pr.fn[3]);
+            fp.ry = make_float4(pr.fn[4], pr.fn[5], pr.fn[6], pr.fn[7]);
+            fp.rw = make_float4(pr.fn[8], pr.fn[9], pr.fn[10], pr.fn[11]);
+            fp.k = make_float4(pr.ka, pr.kd, pr.wsafe, pr.fast ? 1.0f : 0.0f);
+            fp.lim = make_float4(-3.0f * vw.hw, 5.0f * vw.hw, -3.0f * vw.hh, 5.0f * vw.hh);
+            fp.wmax = (float)vw.W - 0.5f;
+            fp.hmax = (float)vw.H - 0.5f;
+            fp.pad0 = fp.pad1 = 0;
+            S.fp[slot][q] = fp;
+        }
+        const uint32_t bytes = 12u * d.n;
+        const uint32_t *src = mesh.idx + 3 * d.t0;
+        const bool tma = (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (bytes & 15) == 0;
+        if (!tma)
+            for (uint32_t w = lane; w < 3 * d.n; w += 32) S.idx[slot][w] = __ldg(src + w);
+        __syncwarp();
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive_expect_tx(&S.full[slot], tma ? bytes : 0u);
+            if (tma) bulk_copy_g2s(S.idx[slot], src, bytes, &S.full[slot]);
+        } else {
+            mbar_arrive(&S.full[slot]);
+        }
+    }
+}
+
+// Persistent stage-1 kernel.  Consumers take one triangle at a time: three
+// index words from shared memory, nine position floats from global memory,
+// then for every pair of the item the conservative tiny-triangle cull.
+// Triangles it keeps are queued per warp and run through the exact path 32
+// at a time, so that path never runs with idle lanes.  INST blocks loop over
+// many pairs (Section 3.5, extended to several views): a triangle's data is
+// loaded once for all of them.
+template <bool INST>
+__global__ void __launch_bounds__(s1::kThreads, 3) k_stage1(FrameDev f) {
+    using namespace s1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<INST> &S = *reinterpret_cast<Smem<INST> *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint64_t n_batches = f.hdr->n_batches;
+    const int n_segs = (int)f.hdr->n_segs;
+    const uint32_t tpt = f.tpt;
+    const uint64_t per_item = (uint64_t)kConsumers * tpt;
+
+    if (tid == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(&S.full[s], 32);                 // the producer warp's lanes
+            mbar_init(&S.empty[s], kConsumerWarps);    // one arrival per consumer warp
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {
+        stage1_producer<INST>(f, S, n_batches, n_segs, per_item);
+        return;
+    }
+
+    // Survivors of the fast cull are queued per warp as (triangle, pair,
+    // mesh) and run through the exact path 32 at a time, so that path never
+    // runs with idle lanes.  The queue outlives the items (entries name the
+    // triangle globally) and is emptied only when full and at the end.
+    uint4 *wq = S.wq[warp];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int qn = 0;
+    auto run_exact = [&](uint4 e, bool has) {
+        const MeshDev mesh = f.meshes[has ? e.w : 0u];
+        const uint64_t t = has ? ((uint64_t)e.y << 32 | e.x) : 0;
+        Tri9 p;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) p.v[c] = 0.0f;
+        if (has) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float *q = mesh.pos + 3 * (uint64_t)__ldg(mesh.idx + 3 * t + c);
+                p.v[3 * c] = __ldg(q); p.v[3 * c + 1] = __ldg(q + 1); p.v[3 * c + 2] = __ldg(q + 2);
+            }
+        }
+        exact_triangle(f, mesh, has ? e.z : 0u, t, p, has);
+    };
+    for (int j = 0;; ++j) {
+        const int slot = j % kSlots;
+        if (!mbar_wait(&S.full[slot], (j / kSlots) & 1u)) {
+            if (lane == 0) atomicOr(f.err, kErrTimeout);
+            return;
+        }
+        const Desc d = S.desc[slot];
+        if (d.b >= n_batches) break;
+        const MeshDev mesh = S.mesh[slot];
+        const uint32_t *idx = S.idx[slot];
+        const uint32_t np = INST ? d.npairs : 1u;
+        for (uint32_t k = 0; k < tpt; ++k) {          // uniform trip count: the warp stays converged
+            // three index words from shared memory, nine position floats from
+            // global memory; an index >= V skips the triangle (reported when checking)
+            const uint32_t lt = k * kConsumers + tid;
+            bool valid = lt < d.n;
+            uint32_t i0 = 0, i1 = 0, i2 = 0;
+            if (valid) {
+                i0 = idx[3 * lt]; i1 = idx[3 * lt + 1]; i2 = idx[3 * lt + 2];
+                if (i0 >= mesh.V || i1 >= mesh.V || i2 >= mesh.V) {
+                    if (f.check) atomicOr(f.err, kErrIndex);
+                    valid = false;
+                }
+            }
+            Tri9 p;
+            if (valid) {
+                const float *q0 = mesh.pos + 3 * (uint64_t)i0, *q1 = mesh.pos + 3 * (uint64_t)i1,
+                            *q2 = mesh.pos + 3 * (uint64_t)i2;
+                p.v[0] = __ldg(q0); p.v[1] = __ldg(q0 + 1); p.v[2] = __ldg(q0 + 2);
+                p.v[3] = __ldg(q1); p.v[4] = __ldg(q1 + 1); p.v[5] = __ldg(q1 + 2);
+                p.v[6] = __ldg(q2); p.v[7] = __ldg(q2 + 1); p.v[8] = __ldg(q2 + 2);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 9; ++c) p.v[c] = 0.0f;
+            }
+            const uint64_t t = d.t0 + lt;
+            for (uint32_t pi = 0; pi < np; ++pi) {
+                const bool live = valid && !fast_cull(S.fp[slot][pi], p);
+                if (f.stats && valid) {
+                    if (live) stat_add(f, kStatFast, 1);
+                    else stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, live);
+                if (m) {
+                    if (live)
+                        wq[qn + __popc(m & lt_mask)] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), d.pair0 + pi, d.mesh);
+                    qn += __popc(m);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        qn -= 32;
+                        run_exact(wq[qn + lane], true);
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+        // the slot is free once every consumer warp is done with it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[slot]);
+    }
+    if (qn > 0) run_exact(wq[lane < (unsigned)qn ? lane : 0], lane < (unsigned)qn);
+}

@@ -58,7 +58,7 @@ def test_small_workload_bit_exact_and_resolve(api, small):
 @pytest.mark.parametrize("cfg", [
     dict(stage1_max_pixels=1), dict(stage1_max_pixels=1024, stage2_max_pixels=32),
     dict(stage2_max_pixels=1 << 30), dict(tile_log2=4), dict(tile_log2=7),
-    dict(stage1_tri_per_thread=1), dict(stage1_tri_per_thread=32),
+    dict(stage1_tri_per_thread=1), dict(stage1_tri_per_thread=3),
     dict(queue1_capacity=1, queue2_capacity=1), dict(queue1_capacity=7, queue2_capacity=3),
 ])
 def test_stage_choices_never_change_visibility(api, small, cfg):
