@@ -58,6 +58,7 @@ typedef int32_t curast_status;
 #define CURAST_ERR_NOT_AFFINE           -7  /* view/model last row not 0 0 0 1  */
 #define CURAST_ERR_BAD_CAMERA           -8  /* proj is not symmetric perspective*/
 #define CURAST_ERR_NOT_BUILT            -9  /* no kernel image for this device  */
+#define CURAST_ERR_TOO_LARGE           -10  /* over a fixed capacity of curast_render_static */
 
 typedef struct curast_ctx curast_ctx;
 
@@ -246,6 +247,41 @@ curast_status curast_stage_times(curast_ctx *ctx, float out[4]);
  * The views' buffers are overwritten. */
 curast_status curast_autotune(curast_ctx *ctx, const curast_view *views, int n_views, curast_stream stream,
                               curast_config *chosen);
+
+/* ------------------------------------------------- no-allocation render --- */
+
+/* The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate device memory -- code running while a CUDA graph is being
+ * captured, real-time loops that must not allocate, hosts that hand out
+ * device memory only from their own pools.
+ *
+ * Renders n_instances (1..CURAST_STATIC_MAX_INSTANCES) instances of one mesh
+ * into one view, like curast_render with the same mesh and instances, and
+ * with bit-identical results, but without a context and without allocating:
+ *   pos, V, idx, T   as in curast_upload_mesh (device buffers)
+ *   models           host, n_instances row-major affine 4x4 matrices, or
+ *                    NULL for one identity instance (n_instances must be 1);
+ *                    instance i owns ids i*T .. i*T + T - 1
+ *   view, proj, W, H, vis, stream   as in curast_render (vis is cleared first)
+ * The pipeline's scratch (frame tables, counters, stage queues) is one fixed
+ * array of about 2 MB in the library's device memory, which every GPU that
+ * loads the library holds until the process exits.  Consequences:
+ *   - the first call on a device looks the array's address up (and sets the
+ *     kernels' shared-memory limits); make that first call before any stream
+ *     capture;
+ *   - every call uses the same array and leaves its contents behind (the
+ *     counters are cleared at the start of each call): calls that overlap on
+ *     the GPU -- on two streams, or from two host threads -- race and corrupt
+ *     each other's frames; serialize them;
+ *   - indices >= V are skipped but not reported (no context to latch them);
+ *   - the stage-1 cull runs its exact path for every triangle (no mesh
+ *     bounds are computed), so it is slower than curast_render.
+ * Fails with CURAST_ERR_TOO_LARGE for n_instances outside 1..32 or V, T at
+ * or above 2^32. */
+#define CURAST_STATIC_MAX_INSTANCES 32
+curast_status curast_render_static(const float *pos, uint64_t V, const uint32_t *idx, uint64_t T,
+                                   const float *models, int n_instances, const float view[16],
+                                   const float proj[16], int W, int H, uint64_t *vis, curast_stream stream);
 
 #ifdef __cplusplus
 }

@@ -21,12 +21,14 @@ STATUS_NAMES = {
     0: "CURAST_OK", -1: "CURAST_ERR_INVALID_ARG", -2: "CURAST_ERR_OUT_OF_MEMORY", -3: "CURAST_ERR_ID_SPACE_OVERFLOW",
     -4: "CURAST_ERR_INDEX_OUT_OF_RANGE", -5: "CURAST_ERR_DEVICE_TIMEOUT", -6: "CURAST_ERR_CUDA",
     -7: "CURAST_ERR_NOT_AFFINE", -8: "CURAST_ERR_BAD_CAMERA", -9: "CURAST_ERR_NOT_BUILT",
+    -10: "CURAST_ERR_TOO_LARGE",
 }
+STATIC_MAX_INSTANCES = 32
 EXPORTS = ["curast_create", "curast_destroy", "curast_status_string", "curast_get_config", "curast_set_config",
            "curast_upload_mesh", "curast_update_mesh", "curast_add_instance", "curast_clear_instances",
            "curast_clear", "curast_render", "curast_render_mesh", "curast_render_batch", "curast_resolve",
            "curast_interpolate", "curast_interpolate_backward", "curast_sync", "curast_stage_times",
-           "curast_autotune", "curast_last_frame"]
+           "curast_autotune", "curast_last_frame", "curast_render_static"]
 
 
 class CurastError(RuntimeError):
@@ -107,6 +109,7 @@ def load(build: bool = False, path: Optional[str] = None) -> C.CDLL:
             "curast_sync": [vp, vp, C.POINTER(Stats)],
             "curast_stage_times": [vp, fp],
             "curast_last_frame": [vp, C.POINTER(FrameInfo)],
+            "curast_render_static": [vp, u64, vp, u64, fp, i32, fp, fp, i32, i32, vp, vp],
             "curast_autotune": [vp, C.POINTER(View), i32, vp, C.POINTER(Config)],
         }
         for name, args in sig.items():
@@ -325,6 +328,30 @@ class Renderer:
         cfg = Config()
         _check(self.L.curast_autotune(self._h, arr, len(full), _stream(stream), C.byref(cfg)), "curast_autotune")
         return cfg.as_dict()
+
+
+def render_static(pos: torch.Tensor, idx: torch.Tensor, models, view, proj, W: int, H: int,
+                  vis: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Context-free render of up to 32 instances of one mesh that allocates no
+    device memory in the library (curast_render_static): for callers that must
+    not allocate, e.g. while a CUDA graph is being captured.  ``models`` is a
+    sequence of 4x4 matrices or None (one identity instance).  All calls share
+    one fixed scratch array, so calls must not overlap on the GPU; the first
+    call on a device should happen before any stream capture."""
+    L = load()
+    if not (pos.is_cuda and idx.is_cuda and pos.dtype == torch.float32 and pos.is_contiguous() and idx.is_contiguous()):
+        raise ValueError("pos must be a contiguous CUDA float32 tensor and idx a contiguous CUDA uint32 tensor")
+    if vis is None:
+        vis = torch.empty((H, W), dtype=torch.int64, device=pos.device)
+    if models is None:
+        mats, n = None, 1
+    else:
+        arr = np.ascontiguousarray(np.stack([np.asarray(m, np.float32).reshape(16) for m in models]), np.float32)
+        n = arr.shape[0]
+        mats = (C.c_float * (16 * n))(*[float(x) for x in arr.reshape(-1)])
+    _check(L.curast_render_static(_ptr(pos), pos.shape[0], _ptr(idx), idx.shape[0], mats, n, _mat(view), _mat(proj),
+                                  W, H, _ptr(vis), _stream(stream)), "curast_render_static")
+    return vis
 
 
 class InterpolateFn(torch.autograd.Function):

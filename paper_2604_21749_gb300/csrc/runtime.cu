@@ -583,6 +583,7 @@ const char *curast_status_string(curast_status s) {
     case CURAST_ERR_NOT_AFFINE: return "matrix is not affine";
     case CURAST_ERR_BAD_CAMERA: return "projection is not a symmetric perspective matrix";
     case CURAST_ERR_NOT_BUILT: return "no kernel image for this device";
+    case CURAST_ERR_TOO_LARGE: return "exceeds a fixed capacity of the no-allocation render";
     default: return "unknown status";
     }
 }
