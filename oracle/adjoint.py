@@ -90,6 +90,26 @@ def barycentrics_closed_form(pos, idx, mv, fx, fy, W, H, tri):
     return D / D.sum(1, keepdims=True)
 
 
+def loss_at_pixels64(pos, idx, col, mv, fx, fy, W, H, pix, tri_pix, target_pix) -> float:
+    """L restricted to the listed pixels (flat indices y*W+x showing triangle
+    tri_pix): the same per-pixel formula as forward64, for local finite
+    differences where a vertex moves only the pixels of its triangles."""
+    pix = np.asarray(pix)
+    x = (pix % W).astype(np.float64)
+    y = (pix // W).astype(np.float64)
+    r = np.stack([((2.0 * x + 1.0) / W - 1.0) / fx, ((2.0 * y + 1.0) / H - 1.0) / fy, -np.ones_like(x)], 1)
+    I, v, _ = _gather(pos, idx, mv, np.asarray(tri_pix))
+    e1, e2, tv = v[1] - v[0], v[2] - v[0], -v[0]
+    pv = np.cross(r, e2)
+    det = np.einsum("ij,ij->i", e1, pv)
+    u = np.einsum("ij,ij->i", tv, pv) / det
+    w = np.einsum("ij,ij->i", r, np.cross(tv, e1)) / det
+    c = np.asarray(col, np.float64)
+    out = (1.0 - u - w)[:, None] * c[I[:, 0]] + u[:, None] * c[I[:, 1]] + w[:, None] * c[I[:, 2]]
+    d = out - np.asarray(target_pix, np.float64)
+    return float((d * d).sum())
+
+
 def loss64(pos, idx, col, mv, fx, fy, W, H, tri, target) -> float:
     out, _, _ = forward64(pos, idx, col, mv, fx, fy, W, H, tri)
     d = out - np.asarray(target, np.float64).reshape(out.shape)
