@@ -166,7 +166,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("raster.cu", "device.cuh"):
+    for f in ("raster.cu", "stage1.cuh", "device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2604_21749_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
