@@ -165,9 +165,15 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the stage kernels' source code with comments and blank space
+    removed (edits to comments do not change the kernel)."""
+    import re
     h = hashlib.sha256()
     for f in ("raster.cu", "stage1.cuh", "device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2604_21749_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2604_21749_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -3,11 +3,11 @@
  *
  * The calls follow the paper's statement of the problem (Schuetz, Lipp,
  * Kristmann, Wimmer: "CuRast: Cuda-Based Software Rasterization for Billions
- * of Triangles"): indexed meshes and their instances (Section 3, "Method";
- * Section 3.5 "Instancing") are rasterized by brute force into a 64-bit
+ * of Triangles"): indexed meshes and their instances (Section 4, "Method";
+ * Section 4.5 "Instancing") are rasterized by brute force into a 64-bit
  * visibility buffer holding 28 depth bits and a 36-bit global triangle id
- * (Section 3.1 "Rasterization"), which a screen pass then resolves into
- * colours (Section 3.4).
+ * (Section 4.1 "Rasterization"), which a screen pass then resolves into
+ * colours (Section 4.4).
  *
  * Conventions for every call
  *   - Pointers marked "device" are CUDA device pointers on the context's
@@ -27,7 +27,7 @@
  *     id; an empty pixel holds 0xFFFFFFFFFFFFFFFF.
  *   - Global id of triangle t of instance i = base[i] + t, where base is the
  *     exclusive prefix sum of the triangle counts of all instances in the
- *     order they were added (Section 3, host frame setup; Section 3.4).
+ *     order they were added (Section 4, host frame setup; Section 4.4).
  *   - Work is enqueued on the given CUDA stream (NULL = legacy default
  *     stream) and the call returns without waiting for the GPU.  Inputs
  *     must stay valid and unmodified until the stream reaches the work.
@@ -126,8 +126,8 @@ curast_status curast_set_config(curast_ctx *ctx, const curast_config *cfg);
 
 /* ------------------------------------------------------- scene objects --- */
 
-/* Registers an indexed triangle mesh (Section 3: indexed meshes; Section
- * 3.1: only indices and positions are read while rasterizing).
+/* Registers an indexed triangle mesh (Section 4: indexed meshes; Section
+ * 4.1: only indices and positions are read while rasterizing).
  *   pos    device, V x 3 FP32 (x, y, z), 4-byte aligned
  *   idx    device, T x 3 uint32 vertex indices, triangles wound CCW = front
  *   rgba8  device, V x 4 bytes of vertex colour for curast_resolve, or NULL
@@ -142,7 +142,7 @@ curast_status curast_upload_mesh(curast_ctx *ctx, const float *pos, uint64_t V, 
 curast_status curast_update_mesh(curast_ctx *ctx, uint32_t mesh_id, const float *pos, const uint32_t *idx,
                                  const uint8_t *rgba8);
 
-/* Adds an instance of a mesh with an affine model matrix (Section 3.5).
+/* Adds an instance of a mesh with an affine model matrix (Section 4.5).
  * Its ids start at the running total of triangles of the instances added
  * before it.  Fails with CURAST_ERR_ID_SPACE_OVERFLOW when the total would
  * exceed 2^36 - 1 triangles. */
@@ -157,7 +157,7 @@ curast_status curast_clear_instances(curast_ctx *ctx);
 /* Fills a visibility buffer with 0xFF..FF (device, n words). */
 curast_status curast_clear(uint64_t *vis, uint64_t n, curast_stream stream);
 
-/* One frame of every instance into one view (Section 3: host setup, then
+/* One frame of every instance into one view (Section 4: host setup, then
  * stages 1, 2 and 3): clears vis, then for every triangle of every instance
  * whose bounds intersect the view frustum keeps, per pixel, the minimum
  * visibility word of the covered fragments.  vis: device, W*H words,
@@ -171,7 +171,7 @@ curast_status curast_render_mesh(curast_ctx *ctx, uint32_t mesh_id, const float 
                                  const float proj[16], int W, int H, uint64_t *vis, curast_stream stream);
 
 /* Batched frame: every instance into every view in ONE persistent launch
- * sequence (Section 3.1 "Looping Through Batches", Section 3.5 extended to
+ * sequence (Section 4.1 "Looping Through Batches", Section 4.5 extended to
  * several views: each triangle is loaded once and rasterized into every
  * (instance, view) pair whose bounds meet that view).  Clears every view's
  * buffer first.  With use_graph = 1 the launch sequence is captured once in
@@ -183,7 +183,7 @@ curast_status curast_render_batch(curast_ctx *ctx, const curast_view *views, int
 
 /* ------------------------------------------------------------ resolve --- */
 
-/* Screen pass (Section 3.4): per pixel, decode the id, find its instance by
+/* Screen pass (Section 4.4): per pixel, decode the id, find its instance by
  * binary search of the prefix sum, fetch the triangle, intersect the pixel
  * centre ray with it in view space and interpolate the RGBA8 vertex colours
  * (c = byte / 255).  rgba_f32: device W*H*4 floats or NULL; rgba8: device
@@ -196,7 +196,7 @@ curast_status curast_resolve(curast_ctx *ctx, const float view[16], const float 
 /* --------------------------------------------------- differentiable step --- */
 
 /* Forward of the differentiable interpolation (perspective-correct
- * barycentrics of Section 3.4 applied to a float attribute): for pixels
+ * barycentrics of Section 4.4 applied to a float attribute): for pixels
  * whose triangle belongs to an instance of mesh_id,
  * out[p] = sum_k b_k(p) attr[v_k]; other pixels get 0.
  *   pos   device V x 3 positions to use instead of the registered ones, or NULL

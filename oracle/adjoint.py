@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see oracle.py).
 
 With the visibility buffer held fixed, every covered pixel p shows one
 triangle (v0, v1, v2) of the mesh, in view space v_k = M p_k + t.  Following
-Section 3.4 (shading in world/view space from the barycentrics of the pixel
+Section 4.4 (shading in world/view space from the barycentrics of the pixel
 ray and the triangle), the pixel ray through the pixel centre is
 r = (ndx / fx, ndy / fy, -1) with ndx = (2x + 1) / W - 1, and the image is
 

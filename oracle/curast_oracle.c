@@ -13,20 +13,20 @@
  * What it computes (paper = Schuetz et al., "CuRast", 2026):
  *   - the visibility buffer: for every pixel the minimum over all covered
  *     fragments of the 64-bit word  depth28 << 36 | global triangle id
- *     (Section 3.1 "Rasterization": 28 depth bits taken from the FP32 depth
- *     by dropping the sign bit and 3 mantissa bits, 36 ID bits; Section 2.1:
+ *     (Section 4.1 "Rasterization": 28 depth bits taken from the FP32 depth
+ *     by dropping the sign bit and 3 mantissa bits, 36 ID bits; Section 3.1:
  *     the closest fragment wins through a 64-bit minimum);
  *   - global triangle ids from the exclusive prefix sum of triangle counts
- *     over the instance list (Section 3, host frame setup; Section 3.4);
+ *     over the instance list (Section 4, host frame setup; Section 4.4);
  *   - view-space transform, projection by the element-wise vector
- *     P = [f/aspect, f, -1] and division of x, y by depth (Section 3.1,
+ *     P = [f/aspect, f, -1] and division of x, y by depth (Section 4.1,
  *     Eq. 1 and Eq. 2);
- *   - near-plane handling by Sutherland-Hodgman clipping (Section 3.2);
- *   - bounding-box scan over pixel centres (Section 3.1 "Rasterization");
- *   - backface culling (Section 3.1);
+ *   - near-plane handling by Sutherland-Hodgman clipping (Section 4.2);
+ *   - bounding-box scan over pixel centres (Section 4.1 "Rasterization");
+ *   - backface culling (Section 4.1);
  *   - the resolve pass: binary search of the prefix sum, per-pixel
  *     barycentrics of the pixel ray and the triangle in view space, and
- *     vertex-colour interpolation (Section 3.4).
+ *     vertex-colour interpolation (Section 4.4).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   R1 coverage is exact integer arithmetic on vertices snapped to 1/256 px,
@@ -116,7 +116,7 @@ void orc_model_view(const float view[16], const float model[16], float mv[12])
         }
 }
 
-/* Section 3.1: transform a vertex to view space (row r of MV applied as
+/* Section 4.1: transform a vertex to view space (row r of MV applied as
  * ((m0*x + m1*y) + m2*z) + m3), then form the clip-space triple. */
 static void view_space(const float mv[12], const float *p, float v[3])
 {
@@ -451,7 +451,7 @@ static uint64_t upper_bound_u64(const uint64_t *a, int n, uint64_t key)
     return (uint64_t)lo;
 }
 
-/* Section 3.4: pixel -> (instance, triangle) by binary search of the prefix
+/* Section 4.4: pixel -> (instance, triangle) by binary search of the prefix
  * sum, then the barycentrics of the pixel-centre ray with the triangle in
  * view space (camera at the origin; Moeller-Trumbore form, unclamped).
  * Returns 0 for background, 1 otherwise. */

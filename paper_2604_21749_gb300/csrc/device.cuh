@@ -115,7 +115,7 @@ constexpr unsigned kErrTimeout = 2u;   // a bounded wait on a bulk copy gave up
 // ------------------------------------------------------------ transform --
 struct CV { float x, y, w; };   // clip-space vertex: fx*vx, fy*vy, -vz
 
-// Section 3.1: view-space transform, each row as ((m0 x + m1 y) + m2 z) + m3,
+// Section 4.1: view-space transform, each row as ((m0 x + m1 y) + m2 z) + m3,
 // then the projection vector of Eq. 2 (x, y scaled by fx, fy; depth = -z).
 __device__ __forceinline__ CV to_clip(const float *mv, float x, float y, float z, float fx, float fy) {
     float vx = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(mv[0], x), __fmul_rn(mv[1], y)), __fmul_rn(mv[2], z)), mv[3]);
@@ -163,7 +163,7 @@ __device__ __forceinline__ CV intersect(CV in, CV out, float fin, float fout, in
     return r;
 }
 
-// Sutherland-Hodgman (Section 3.2) against near, left, right, bottom, top.
+// Sutherland-Hodgman (Section 4.2) against near, left, right, bottom, top.
 // Returns 0 or the vertex count (3..8); a triangle inside every plane comes
 // back unchanged.
 static __device__ __noinline__ int clip_polygon(const CV tri[3], float nearv, CV out[kMaxPoly]) {
@@ -251,7 +251,7 @@ __device__ __forceinline__ bool setup_subtri(SubTri &s, int W, int H) {
     return true;
 }
 
-// Depth (Section 3.1, perspective-correct): A / sum_k float(E_k) * iz_k, the
+// Depth (Section 4.1, perspective-correct): A / sum_k float(E_k) * iz_k, the
 // sum taken as (t0 + t1) + t2; then the 64-bit word depth28 << 36 | id.
 __device__ __forceinline__ uint64_t frag_key(int64_t E0, int64_t E1, int64_t E2, int64_t A, const float iz[3],
                                              uint64_t id) {
@@ -261,7 +261,7 @@ __device__ __forceinline__ uint64_t frag_key(int64_t E0, int64_t E1, int64_t E2,
     return ((uint64_t)(__float_as_uint(depth) >> 3) << 36) | (id & kIdMask);
 }
 
-// Section 2.1: the closest fragment wins by a 64-bit atomic minimum.  A
+// Section 3.1: the closest fragment wins by a 64-bit atomic minimum.  A
 // plain read first skips the atomic when the stored word is already
 // smaller (words only ever decrease, so a stale read is still safe).
 __device__ __forceinline__ void depth_test_write(uint64_t *vis, size_t pix, uint64_t key) {
@@ -281,7 +281,7 @@ __device__ __forceinline__ void shade_pixel(const SubTri &s, int x, int y, uint6
 }
 
 // Pixels i = start, start + stride, ... of the sub-triangle's pixel range
-// (x = x0 + i mod w, y = y0 + i / w: the 1D loop of Section 3.2), optionally
+// (x = x0 + i mod w, y = y0 + i / w: the 1D loop of Section 4.2), optionally
 // restricted to a sub-rectangle.
 __device__ __forceinline__ void raster_range(const SubTri &s, int x0, int x1, int y0, int y1, int start, int stride,
                                              uint64_t *vis, int W) {

@@ -1,10 +1,10 @@
-// raster.cu -- clear, stage 1, stage 2 and stage 3 kernels (Section 3.1-3.3).
+// raster.cu -- clear, stage 1, stage 2 and stage 3 kernels (Section 4.1-3.3).
 #include "internal.h"
 
 namespace curast {
 
 // ------------------------------------------------------------------ clear --
-// Section 3.1: the framebuffer starts each frame at the empty word (all
+// Section 4.1: the framebuffer starts each frame at the empty word (all
 // ones, larger than any fragment).  16-byte stores, grid-stride.
 __global__ void __launch_bounds__(256) k_clear(uint64_t *vis, uint64_t n) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -94,7 +94,7 @@ __device__ __forceinline__ void q1_append(const FrameDev &f, bool want, uint64_t
 }
 
 // ---------------------------------------------------------------- stage 1 --
-// Small-triangle rasterizer of Section 3.1: one thread per triangle, y outer
+// Small-triangle rasterizer of Section 4.1: one thread per triangle, y outer
 // / x inner over the bounding box with incrementally updated edge functions.
 // int32 is exact here because both bbox extents are below 2^14 subpixels,
 // so |E| < 2^30 at every visited sample.
@@ -183,7 +183,7 @@ __device__ __forceinline__ int classify(const FrameDev &f, const Rec r[3], const
 #include "stage1.cuh"
 
 // ---------------------------------------------------------------- stage 2 --
-// Section 3.2: one warp per queued triangle.  The triangle is clipped
+// Section 4.2: one warp per queued triangle.  The triangle is clipped
 // (Sutherland-Hodgman, near plane and guard band) and fan-triangulated;
 // sub-triangles with a bbox of at most s2_max pixels are rasterized by the
 // warp with the 1D pixel loop, larger ones are split along tile boundaries
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) k_stage2(FrameDev f) {
 }
 
 // ---------------------------------------------------------------- stage 3 --
-// Section 3.3: one block per tile part; its threads walk the tile's pixels
+// Section 4.3: one block per tile part; its threads walk the tile's pixels
 // (restricted to the sub-triangle's bbox) line by line.
 __global__ void __launch_bounds__(256) k_stage3(FrameDev f) {
     __shared__ unsigned long long s_i;

@@ -1,6 +1,6 @@
 // runtime.cu -- host runtime behind include/curast.h.
 //
-// Frame setup follows Section 3 ("On the host side, before launching the
+// Frame setup follows Section 4 ("On the host side, before launching the
 // rasterization stages"): per (instance, view) frustum culling against the
 // mesh bounds, the list of meshes with their transformation matrices, the
 // exclusive prefix sum of triangle counts for the global ids, and a copy of

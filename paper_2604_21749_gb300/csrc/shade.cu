@@ -1,10 +1,10 @@
-// shade.cu -- resolve pass (Section 3.4) and the differentiable interpolation
+// shade.cu -- resolve pass (Section 4.4) and the differentiable interpolation
 // step (forward and backward) on a fixed visibility buffer.
 #include "internal.h"
 
 namespace curast {
 
-// view-space vertex: row r of MV as ((m0 x + m1 y) + m2 z) + m3 (Section 3.1)
+// view-space vertex: row r of MV as ((m0 x + m1 y) + m2 z) + m3 (Section 4.1)
 __device__ __forceinline__ float3 view_space(const float *m, const float *p) {
     float3 v;
     v.x = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[0], p[0]), __fmul_rn(m[1], p[1])), __fmul_rn(m[2], p[2])), m[3]);
@@ -31,7 +31,7 @@ __device__ __forceinline__ float interp3(float b0, float b1, float b2, float c0,
     return __fadd_rn(__fadd_rn(__fmul_rn(b0, c0), __fmul_rn(b1, c1)), __fmul_rn(b2, c2));
 }
 
-// Section 3.4: the mesh instance owning a global id is found by binary
+// Section 4.4: the mesh instance owning a global id is found by binary
 // search of the exclusive prefix sum (last instance with base <= id).
 __device__ __forceinline__ int find_instance(const uint64_t *base, int n, uint64_t id) {
     int lo = 0, hi = n;   // first index with base[i] > id

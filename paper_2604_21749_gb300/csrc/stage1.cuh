@@ -1,4 +1,4 @@
-// stage1.cuh -- the persistent stage-1 kernel (Section 3.1), included by raster.cu.
+// stage1.cuh -- the persistent stage-1 kernel (Section 4.1), included by raster.cu.
 //
 // Warp-specialized pipeline: one producer warp grabs work items from the
 // global counter, stages each item's index triples in shared memory with a
@@ -74,7 +74,7 @@ struct __align__(16) FastPair {
 
 struct Tri9 { float v[9]; };    // the three vertices of a triangle, passed by value
 
-// The "bbox holds no pixel centre" test of Section 3.1, done before the
+// The "bbox holds no pixel centre" test of Section 4.1, done before the
 // exact arithmetic: the estimated bbox widened by the error bound must hold
 // no pixel centre of the screen while every vertex lies safely in front of
 // the near plane and inside the window -- then the exact snapped bbox holds
@@ -174,7 +174,7 @@ struct Smem {
 template <bool INST>
 size_t stage1_smem_bytes() { return sizeof(s1::Smem<INST>); }
 
-// Producer warp: work grabs (Section 3.1 "Looping Through Batches": a
+// Producer warp: work grabs (Section 4.1 "Looping Through Batches": a
 // global counter hands out items until all triangles are done; the counter
 // is read one grab ahead), the forward search for the item's segment, the
 // item's pair constants, and the TMA copy of its index triples.
@@ -276,7 +276,7 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
 // then for every pair of the item the conservative tiny-triangle cull.
 // Triangles it keeps are queued per warp and run through the exact path 32
 // at a time, so that path never runs with idle lanes.  INST blocks loop over
-// many pairs (Section 3.5, extended to several views): a triangle's data is
+// many pairs (Section 4.5, extended to several views): a triangle's data is
 // loaded once for all of them.
 template <bool INST>
 __global__ void __launch_bounds__(s1::kThreads, 3) k_stage1(FrameDev f) {

@@ -1,7 +1,7 @@
 """Seeded scene generators (heightfields, displaced spheres, instances, cameras).
 
 The paper evaluates on photogrammetry scans (Sponza, Lantern, Komainu Kobe,
-Venice, Zorah; Section 4, Table 1) that are not available here.  These
+Venice, Zorah; Section 5, Table 1) that are not available here.  These
 generators stand in for them with the same structure: dense, opaque, indexed
 triangle meshes with uint32 indices, FP32 xyz positions, RGBA8 vertex colours,
 and row-major vertex/triangle order (the locality a mesh optimizer produces).
