@@ -8,6 +8,7 @@ adjoint.  A dropped term, a flipped sign, a transposed operand or a wrong
 index anywhere in the oracle fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -210,6 +211,31 @@ def test_full_viewport_quad_covers_w_times_h(oracle_lib):
     q = np.array([[0, 0, 256 * W, 0, 0, 256 * H], [256 * W, 0, 256 * W, 256 * H, 0, 256 * H]], np.int32)
     cnt = O.raster_fixed(q, np.ones((2, 3), np.float32), W, H, mode=1)
     assert (cnt == 1).all() and int(cnt.sum()) == W * H
+
+
+def _golden_rows(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    with open(path) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.lstrip().startswith("#")]
+
+
+def test_visibility_word_golden(oracle_lib):
+    """Words of fragments at exactly known depths match the hand-derived
+    values of tests/golden/visibility_word.txt (28 depth bits over 36 id
+    bits, Section 4.1), and the closer fragment wins in either order."""
+    O = oracle_lib
+    tri = np.array([[0, 0, 2048, 0, 0, 2048]], np.int32)     # covers every centre of 4x4
+    rows = _golden_rows("visibility_word.txt")
+    assert len(rows) == 6
+    for iz, tid, word in rows:
+        vis = O.raster_fixed(tri, np.full((1, 3), float(iz), np.float32), 4, 4, id0=int(tid))
+        assert (vis == np.uint64(int(word, 16))).all(), (iz, tid, hex(int(vis[0, 0])))
+    # depth 1 (iz 1) beats depth 2 (iz 0.5) whichever of the two comes first
+    two = np.concatenate([tri, tri])
+    for izs, want in (([0.5, 1.0], 0x7F00000000000001), ([1.0, 0.5], 0x7F00000000000000)):
+        iz = np.array([[izs[0]] * 3, [izs[1]] * 3], np.float32)
+        vis = O.raster_fixed(two, iz, 4, 4, id0=0)
+        assert (vis == np.uint64(want)).all(), hex(int(vis[0, 0]))
 
 
 # -------------------------------------------------------------- end to end ---
