@@ -80,12 +80,15 @@ typedef struct {
     uint32_t stage1_max_pixels;  /* stage 1 rasterizes bbox <= this (paper: 128), 1..1024   */
     uint32_t stage2_max_pixels;  /* stage 2 rasterizes bbox <= this (paper: 4096), >= 32     */
     uint32_t tile_log2;          /* stage-3 tile side 2^k px (paper: 64 -> 6), 4..7          */
-    uint32_t stage1_tri_per_thread; /* triangles per thread per stage-1 work grab, 1..32     */
+    uint32_t stage1_tri_per_thread; /* triangles per thread per stage-1 work grab, 1..4      */
     uint32_t pairs_per_segment;  /* instance-view pairs one stage-1 work item loops over     */
     uint64_t queue1_capacity;    /* stage 1 -> 2 queue entries; overflow is rasterized in place */
     uint64_t queue2_capacity;    /* stage 2 -> 3 tile parts;   overflow is rasterized in place */
     uint32_t check_indices;      /* 1: bounds-check every index on the device               */
     uint32_t collect_stats;      /* 1: count culled / forwarded triangles (slower)           */
+    uint64_t stage1_bitmap_bytes; /* survivor bitmap of the stage-1 cull (1 bit per triangle x
+                                    pair); a frame needing more runs stage 1 in several
+                                    rounds, 2^12..2^36                                       */
 } curast_config;
 
 /* Counters read back by curast_sync.  Stats fields are filled only when
@@ -225,6 +228,7 @@ typedef struct {
     uint64_t triangles;          /* sum over pairs of the mesh's triangle count           */
     uint64_t unique_triangles;   /* sum of T over meshes with at least one pair           */
     uint64_t unique_vertices;    /* sum of V over the same meshes                         */
+    uint64_t rounds;             /* stage-1 rounds (cull + exact kernel pairs)            */
 } curast_frame_info;
 
 curast_status curast_last_frame(const curast_ctx *ctx, curast_frame_info *out);
@@ -237,8 +241,9 @@ curast_status curast_last_frame(const curast_ctx *ctx, curast_frame_info *out);
 curast_status curast_sync(curast_ctx *ctx, curast_stream stream, curast_stats *stats);
 
 /* Per-stage device times (ms) of the last render issued on this context:
- * out[0] clear, [1] stage 1, [2] stage 2, [3] stage 3; waits for them. */
-curast_status curast_stage_times(curast_ctx *ctx, float out[4]);
+ * out[0] clear, [1] stage-1 cull, [2] stage-1 exact path, [3] stage 2,
+ * [4] stage 3; waits for them. */
+curast_status curast_stage_times(curast_ctx *ctx, float out[5]);
 
 /* Picks stage thresholds, tile size and batch shape for the given views by
  * timing candidate configurations with curast_render_batch.  A candidate is

@@ -47,7 +47,7 @@ class Config(C.Structure):
     _fields_ = [("stage1_max_pixels", C.c_uint32), ("stage2_max_pixels", C.c_uint32), ("tile_log2", C.c_uint32),
                 ("stage1_tri_per_thread", C.c_uint32), ("pairs_per_segment", C.c_uint32),
                 ("queue1_capacity", C.c_uint64), ("queue2_capacity", C.c_uint64), ("check_indices", C.c_uint32),
-                ("collect_stats", C.c_uint32)]
+                ("collect_stats", C.c_uint32), ("stage1_bitmap_bytes", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,7 +66,8 @@ class Stats(C.Structure):
 
 class FrameInfo(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("segments", C.c_uint64), ("work_items", C.c_uint64),
-                ("triangles", C.c_uint64), ("unique_triangles", C.c_uint64), ("unique_vertices", C.c_uint64)]
+                ("triangles", C.c_uint64), ("unique_triangles", C.c_uint64), ("unique_vertices", C.c_uint64),
+                ("rounds", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -318,7 +319,9 @@ class Renderer:
         return fi.as_dict()
 
     def stage_times(self) -> List[float]:
-        out = (C.c_float * 4)()
+        """Milliseconds of the last render: clear, stage-1 cull, stage-1
+        exact, stage 2, stage 3."""
+        out = (C.c_float * 5)()
         _check(self.L.curast_stage_times(self._h, out), "curast_stage_times")
         return list(out)
 

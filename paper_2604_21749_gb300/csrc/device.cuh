@@ -29,13 +29,15 @@ struct ViewDev {             // one view of a frame
 
 struct PairDev {             // one (instance, view) pair that survived host culling
     float mv[12];            // rows 0..2 of view * model, FP32 (the exact transform)
-    // conservative tiny-triangle cull: rows giving X*w, Y*w (pixels) and w
-    // with FMA, and the bound on how far that estimate and the exact snapped
-    // position can lie apart: margin = ka * max(1/w) + kd pixels, valid
-    // when every w exceeds wsafe; fast = 0 disables the test
+    // conservative tiny-triangle cull: rows giving X'*w, Y'*w and w with FMA,
+    // where X' = X - 1/2 and Y' = Y - 1/2 put the pixel centres on integers;
+    // the estimate and the exact snapped position lie at most
+    // margin = max(1/w) * (fk0 + fk1 a) + fk2 a + fk3 pixels apart, a the
+    // largest |X'|, |Y'| of the triangle, while every w exceeds wsafe and
+    // every |X'| < winx, |Y'| < winy; wsafe = +inf disables the test
     float fn[12];
-    float ka, kd, wsafe;
-    uint32_t fast;
+    float fk[4];
+    float wsafe, winx, winy;
     uint64_t base;           // global id of the instance's triangle 0
     uint32_t view;
     uint32_t mesh;
@@ -48,7 +50,15 @@ struct SegDev {              // a stage-1 work item: one mesh x a run of its pai
     uint32_t pad;
     uint64_t T;              // triangles of the mesh
     uint64_t batch0;         // first work-grab index of this segment
+    uint64_t word0;          // first survivor-bitmap word of this segment (frame-wide)
 };
+
+// The frame's work items in rounds, each small enough for the survivor
+// bitmap: round r culls items [b0, b1) into bitmap words [w0, w1).
+struct RoundDev {
+    uint64_t b0, b1, w0, w1;
+};
+constexpr int kMaxRounds = 64;
 
 struct MeshDev {
     const float *pos;
@@ -72,7 +82,7 @@ struct Q2Entry {             // stage 2 -> stage 3: one tile of one sub-triangle
 };
 
 struct Counters {
-    unsigned long long work;          // stage-1 work grabs
+    unsigned long long work[kMaxRounds];   // stage-1 work grabs of each round
     unsigned long long q1_count, q1_next;
     unsigned long long q2_count, q2_next;
     unsigned long long overflow1, overflow2;
@@ -88,6 +98,8 @@ struct FrameHdr {
     uint64_t n_batches;      // stage-1 work items
     uint32_t n_segs;
     uint32_t n_views;
+    uint32_t n_rounds;
+    uint32_t pad;
 };
 
 struct FrameDev {
@@ -95,9 +107,11 @@ struct FrameDev {
     const ViewDev *views;
     const PairDev *pairs;
     const SegDev *segs;
+    const RoundDev *rounds;
     const MeshDev *meshes;
     Q1Entry *q1;
     Q2Entry *q2;
+    uint32_t *bits;          // survivor bitmap of the current round (nullptr: fused stage 1)
     Counters *ctr;
     unsigned *err;           // sticky error bits, cleared by curast_sync
     uint64_t q1_cap, q2_cap;

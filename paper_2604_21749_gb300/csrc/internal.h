@@ -7,7 +7,8 @@
 namespace curast {
 
 struct LaunchShape {
-    int stage1_blocks_per_sm[2];   // [single pair, instanced]
+    int stage1_blocks_per_sm[2][2];   // [instanced][fused]
+    int stage1x_blocks_per_sm;        // exact kernel of stage 1
     int stage2_blocks_per_sm;
     int stage3_blocks_per_sm;
     int num_sms;
@@ -16,7 +17,10 @@ struct LaunchShape {
 cudaError_t query_launch_shape(LaunchShape *out, int device);
 
 cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s);
-cudaError_t launch_stage1(const FrameDev &f, bool instanced, int blocks, cudaStream_t s);
+// Stage 1 of round r: the cull kernel (fused: it runs the exact path itself
+// and needs no bitmap), then the exact kernel over the round's bitmap.
+cudaError_t launch_stage1(const FrameDev &f, bool instanced, bool fused, uint32_t r, int blocks, cudaStream_t s);
+cudaError_t launch_stage1_exact(const FrameDev &f, uint32_t r, int blocks, cudaStream_t s);
 cudaError_t launch_stage2(const FrameDev &f, int blocks, cudaStream_t s);
 cudaError_t launch_stage3(const FrameDev &f, int blocks, cudaStream_t s);
 // scratch: 256 * 6 floats; out6: xmin ymin zmin xmax ymax zmax

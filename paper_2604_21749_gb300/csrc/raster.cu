@@ -1,4 +1,4 @@
-// raster.cu -- clear, stage 1, stage 2 and stage 3 kernels (Section 4.1-3.3).
+// raster.cu -- clear, stage 1, stage 2 and stage 3 kernels (Sections 4.1-4.3).
 #include "internal.h"
 
 namespace curast {
@@ -57,21 +57,24 @@ __device__ __forceinline__ void load_clip(const FrameDev &f, const MeshDev &mesh
 }
 
 // queue 1 is full: the thread clips and rasterizes its triangle itself.
-// (Out-of-line helpers take structs by value: a reference to the kernel
-// parameter or to a hot-loop local would force that object into local
-// memory for the whole kernel.)
-__device__ __noinline__ void q1_overflow(FrameDev f, uint64_t id, uint32_t pidx, MeshDev mesh, uint64_t t,
-                                         ViewDev vw) {
+// (Out-of-line helpers take the frame and the mesh by pointer into parameter
+// or global memory: a struct passed by value, or a reference to a local,
+// would be copied to local memory on every call.)
+__device__ __noinline__ void q1_overflow(const FrameDev *fp, uint64_t id, uint32_t pidx, const MeshDev *mesh,
+                                         uint64_t t) {
+    const FrameDev &f = *fp;
     atomicAdd(&f.ctr->overflow1, 1ull);
+    const ViewDev &vw = f.views[f.pairs[pidx].view];
     CV c[3];
-    load_clip(f, mesh, pidx, t, vw, c);
+    load_clip(f, *mesh, pidx, t, vw, c);
     raster_triangle_general(c, vw, id, 0, 1);
 }
 
 // Warp-aggregated append to queue 1 (ballot + popc + one atomicAdd per warp).
 // Lanes whose slot lies beyond the capacity rasterize their triangle in place.
+// f must live in parameter or global memory (its address is passed on).
 __device__ __forceinline__ void q1_append(const FrameDev &f, bool want, uint64_t id, uint32_t pidx,
-                                          const MeshDev &mesh, uint64_t t, const ViewDev &vw) {
+                                          const MeshDev *mesh, uint64_t t) {
     const unsigned active = __activemask();
     const unsigned m = __ballot_sync(active, want);
     if (m == 0) return;
@@ -89,7 +92,7 @@ __device__ __forceinline__ void q1_append(const FrameDev &f, bool want, uint64_t
         e.pad = 0;
         f.q1[slot] = e;
     } else {
-        q1_overflow(f, id, pidx, mesh, t, vw);
+        q1_overflow(&f, id, pidx, mesh, t);
     }
 }
 
@@ -342,17 +345,22 @@ __global__ void k_aabb_final(const float *part, int n, float *out) {
 }
 
 // -------------------------------------------------------------- launchers --
+template <bool INST, bool FUSED>
+cudaError_t stage1_shape(int *blocks) {
+    const size_t sm = stage1_smem_bytes<INST, FUSED>();
+    cudaError_t e = cudaFuncSetAttribute(k_stage1<INST, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_stage1<INST, FUSED>, s1::kThreads, sm);
+}
+
 cudaError_t query_launch_shape(LaunchShape *o, int device) {
     cudaError_t e = cudaDeviceGetAttribute(&o->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    const size_t sm0 = stage1_smem_bytes<false>(), sm1 = stage1_smem_bytes<true>();
-    e = cudaFuncSetAttribute(k_stage1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_stage1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1_blocks_per_sm[0], k_stage1<false>, s1::kThreads, sm0);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1_blocks_per_sm[1], k_stage1<true>, s1::kThreads, sm1);
+    if ((e = stage1_shape<false, false>(&o->stage1_blocks_per_sm[0][0])) != cudaSuccess) return e;
+    if ((e = stage1_shape<false, true>(&o->stage1_blocks_per_sm[0][1])) != cudaSuccess) return e;
+    if ((e = stage1_shape<true, false>(&o->stage1_blocks_per_sm[1][0])) != cudaSuccess) return e;
+    if ((e = stage1_shape<true, true>(&o->stage1_blocks_per_sm[1][1])) != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1x_blocks_per_sm, k_stage1_exact, 32 * s1::kExactWarps, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage2_blocks_per_sm, k_stage2, 256, 0);
     if (e != cudaSuccess) return e;
@@ -369,9 +377,16 @@ cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_stage1(const FrameDev &f, bool instanced, int blocks, cudaStream_t s) {
-    if (instanced) k_stage1<true><<<blocks, s1::kThreads, stage1_smem_bytes<true>(), s>>>(f);
-    else k_stage1<false><<<blocks, s1::kThreads, stage1_smem_bytes<false>(), s>>>(f);
+cudaError_t launch_stage1(const FrameDev &f, bool instanced, bool fused, uint32_t r, int blocks, cudaStream_t s) {
+    if (instanced && fused) k_stage1<true, true><<<blocks, s1::kThreads, stage1_smem_bytes<true, true>(), s>>>(f, r);
+    else if (instanced) k_stage1<true, false><<<blocks, s1::kThreads, stage1_smem_bytes<true, false>(), s>>>(f, r);
+    else if (fused) k_stage1<false, true><<<blocks, s1::kThreads, stage1_smem_bytes<false, true>(), s>>>(f, r);
+    else k_stage1<false, false><<<blocks, s1::kThreads, stage1_smem_bytes<false, false>(), s>>>(f, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage1_exact(const FrameDev &f, uint32_t r, int blocks, cudaStream_t s) {
+    k_stage1_exact<<<blocks, 32 * s1::kExactWarps, 0, s>>>(f, r);
     return cudaGetLastError();
 }
 

@@ -137,20 +137,22 @@ bool instance_visible(const float *mv, const MeshRec &m, const Cam &cam) {
 }
 
 // Constants of the conservative tiny-triangle cull of one (instance, view).
-// The fast estimate X_f = (fn_x . p) / (fn_w . p) uses FMA and an
+// The estimate X'_f = (fn_x . p) / (fn_w . p) uses FMA rows and an
 // approximate reciprocal; the exact path is the FP32 sequence of the
-// projection (Eq. 2) and the snap.  With S_r = sum_j |m_rj a_j| + |m_r3|
-// (a_j the largest |coordinate| of the mesh bounds) and |s| <= 4, forward
-// error analysis (u = 2^-24, reciprocal error taken as 2^-20) gives
-//   |X_f - X_exact| <= hw u (9 fx S_0 + 40 S_2) / w + hw (5 2^-20 + 25 u) + 1/512,
-// which ka / w + kd below exceeds by a wide factor.  wsafe keeps the exact
-// depth of every vertex above the near plane.
+// projection (Eq. 2) and the snap.  Forward error analysis of both, with
+// S_r = sum_j |m_rj a_j| + |m_r3| (a_j the largest |coordinate| of the mesh
+// bounds), bounds their distance by max(1/w) (ka + kb |X'|) + kc |X'| + kd
+// pixels (the terms are listed below).  wsafe keeps the exact depth of every
+// vertex above the near plane.
 void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     std::memset(p.fn, 0, sizeof(p.fn));
-    p.ka = p.kd = p.wsafe = 0.0f;
-    p.fast = 0;
+    std::memset(p.fk, 0, sizeof(p.fk));
+    p.wsafe = INFINITY;
+    p.winx = p.winy = 0.0f;
     if (!m.bounded) return;
-    const double u = std::ldexp(1.0, -24), er = std::ldexp(1.0, -20);
+    // u: FP32 unit roundoff; rho: relative error assumed for rcp.approx.ftz.f32
+    // (8x the documented one ulp)
+    const double u = std::ldexp(1.0, -24), rho = std::ldexp(1.0, -20);
     double amax[3], S[3];
     for (int j = 0; j < 3; ++j) amax[j] = std::max(std::fabs(m.lo[j]), std::fabs(m.hi[j]));
     for (int r = 0; r < 3; ++r) {
@@ -158,21 +160,36 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
         for (int j = 0; j < 3; ++j) S[r] += std::fabs((double)p.mv[4 * r + j]) * amax[j];
     }
     const double hw = v.hw, hh = v.hh, fx = v.fx, fy = v.fy;
+    const double ax = hw * fx, bx = hw - 0.5, ay = hh * fy, by = hh - 0.5;
     for (int j = 0; j < 4; ++j) {
         const double wr = -(double)p.mv[8 + j];
-        p.fn[j] = (float)(hw * (fx * (double)p.mv[j] + wr));
-        p.fn[4 + j] = (float)(hh * (fy * (double)p.mv[4 + j] + wr));
+        p.fn[j] = (float)(ax * (double)p.mv[j] + bx * wr);
+        p.fn[4 + j] = (float)(ay * (double)p.mv[4 + j] + by * wr);
         p.fn[8 + j] = (float)wr;
     }
-    const double ka = 1.01 * u * std::max(hw * (16 * fx * S[0] + 64 * S[2]), hh * (16 * fy * S[1] + 64 * S[2]));
-    const double kd = std::max(hw, hh) * (8 * er + 64 * u) + 1.0 / 256 + 1.0 / 512;
+    // Error budget per coordinate (pixels), exact path plus estimate:
+    //   (9.002u a S_axis + 4.001u b S_z + 4.001u h S_z + 7.002u (|X'| + 1) S_z) / w
+    //   + (|X'| + 1)(rho + 7.01u) + 5.01u (h + 1) + 1/512 (the snap),
+    // with 1/w <= max(1/w~) (1 + 4u S_z / wsafe) / (1 - rho) for the estimated w~.
     const double ws = v.nearv * (1 + 1e-3) + 8 * u * S[2];
-    if (!std::isfinite(ka) || !std::isfinite(kd) || !std::isfinite(ws) || ka > 1e30 || ws > 1e30) return;
-    // round the constants up so the float copies stay conservative
-    p.ka = (float)(ka * (1 + 1e-6));
-    p.kd = (float)(kd * (1 + 1e-6));
+    const double F = 1.01 * (1 + 4 * u * S[2] / ws) / (1 - rho);
+    const double kax = 9.002 * ax * S[0] + 4.001 * bx * S[2] + 4.001 * hw * S[2] + 7.002 * S[2];
+    const double kay = 9.002 * ay * S[1] + 4.001 * by * S[2] + 4.001 * hh * S[2] + 7.002 * S[2];
+    const double ka = F * u * std::max(kax, kay);
+    const double kb = F * u * 7.002 * S[2];
+    const double kc = 1.01 * (rho + 7.01 * u);
+    const double kd = 1.01 * (5.01 * u * (std::max(hw, hh) + 1) + rho + 7.01 * u) + 1.0 / 512;
+    if (!std::isfinite(ka) || !std::isfinite(ws) || ka > 1e30 || ws > 1e30) return;
+    // round the constants up (the window down) so the float copies stay conservative
+    p.fk[0] = (float)(ka * (1 + 1e-6));
+    p.fk[1] = (float)(kb * (1 + 1e-6));
+    p.fk[2] = (float)(kc * (1 + 1e-6));
+    p.fk[3] = (float)(kd * (1 + 1e-6));
     p.wsafe = (float)(ws * (1 + 1e-6));
-    p.fast = 1;
+    // inside +-4 screen extents every vertex lies far within the guard band
+    // (|X - W/2| <= 128 W/2), so the exact path would not clip it
+    p.winx = (float)(8.0 * hw);
+    p.winy = (float)(8.0 * hh);
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -187,6 +204,7 @@ curast_config default_config() {
     c.pairs_per_segment = 64;
     c.queue1_capacity = 1ull << 22;
     c.queue2_capacity = 1ull << 21;
+    c.stage1_bitmap_bytes = 1ull << 30;
     c.check_indices = 1;
     c.collect_stats = 0;
     return c;
@@ -225,13 +243,15 @@ struct curast_ctx {
     bool instanced = false;
 
     DevBuf<Q1Entry> d_q1;
+    DevBuf<uint32_t> d_bits;              // survivor bitmap of one stage-1 round
+    std::vector<RoundDev> rounds;
     DevBuf<Q2Entry> d_q2;
     Counters *d_ctr = nullptr;
     unsigned *d_err = nullptr;
     float *d_aabb = nullptr;              // 256*6 scratch + 6 result
     unsigned long long *d_diff = nullptr;
 
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool ev_recorded = false;
 
     cudaGraphExec_t gexec = nullptr;
@@ -365,20 +385,55 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
     }
     // heavy work items (many pairs) first so the tail of the persistent loop is light
     std::stable_sort(c->hs.begin(), c->hs.end(), [](const SegDev &a, const SegDev &b) { return a.npairs > b.npairs; });
-    uint64_t nb = 0;
+    // survivor-bitmap words: per item, npairs x (per_item / 32)
+    const uint64_t G = per_item / 32;
+    uint64_t nb = 0, nw = 0;
     c->instanced = false;
     for (SegDev &s : c->hs) {
         s.batch0 = nb;
-        nb += (s.T + per_item - 1) / per_item;
+        s.word0 = nw;
+        const uint64_t items = (s.T + per_item - 1) / per_item;
+        nb += items;
+        nw += items * s.npairs * G;
         c->instanced = c->instanced || s.npairs > 1;
     }
+    // rounds: runs of items whose bitmap fits the configured size (grown
+    // when the frame would need more than kMaxRounds rounds)
+    uint64_t cap = std::max<uint64_t>(c->cfg.stage1_bitmap_bytes / 4, 64 * G);
+    cap = std::max<uint64_t>(cap, (nw + kMaxRounds - 1) / kMaxRounds + 64 * G);
+    c->rounds.clear();
+    RoundDev cur{0, 0, 0, 0};
+    for (const SegDev &s : c->hs) {
+        const uint64_t items = (s.T + per_item - 1) / per_item, wpi = s.npairs * G;
+        uint64_t done = 0;
+        while (done < items) {
+            uint64_t room = (cap - (cur.w1 - cur.w0)) / wpi;
+            if (room == 0) {
+                c->rounds.push_back(cur);
+                cur = RoundDev{cur.b1, cur.b1, cur.w1, cur.w1};
+                room = cap / wpi;
+            }
+            const uint64_t take = std::min(room, items - done);
+            cur.b1 += take;
+            cur.w1 += take * wpi;
+            done += take;
+        }
+    }
+    if (cur.b1 > cur.b0 || c->rounds.empty()) c->rounds.push_back(cur);
+    if (c->rounds.size() > (size_t)kMaxRounds) return CURAST_ERR_INVALID_ARG;   // unreachable by the cap above
+    uint64_t maxw = 1;
+    for (const RoundDev &r : c->rounds) maxw = std::max(maxw, r.w1 - r.w0);
+    CU(c->d_bits.reserve(maxw));
     c->hdr.n_batches = nb;
     c->hdr.n_segs = (uint32_t)c->hs.size();
     c->hdr.n_views = (uint32_t)nv;
+    c->hdr.n_rounds = (uint32_t)c->rounds.size();
+    c->hdr.pad = 0;
     return CURAST_OK;
 }
 
-constexpr size_t kHdrBytes = 256;
+constexpr size_t kRoundsOff = 256;                                        // RoundDev[kMaxRounds]
+constexpr size_t kHdrBytes = kRoundsOff + kMaxRounds * sizeof(RoundDev);   // 2304
 
 size_t off_views(const curast_ctx *) { return kHdrBytes; }
 size_t off_segs(const curast_ctx *c) { return align_up(kHdrBytes + c->cap_views * sizeof(ViewDev), 256); }
@@ -401,6 +456,7 @@ curast_status upload_frame(curast_ctx *c, cudaStream_t s) {
     CU(cudaEventSynchronize(c->ev_tab));
     unsigned char *h = c->h_tab.p;
     std::memcpy(h, &c->hdr, sizeof(FrameHdr));
+    std::memcpy(h + kRoundsOff, c->rounds.data(), c->rounds.size() * sizeof(RoundDev));
     std::memcpy(h + off_views(c), c->hv.data(), c->hv.size() * sizeof(ViewDev));
     std::memcpy(h + off_segs(c), c->hs.data(), c->hs.size() * sizeof(SegDev));
     std::memcpy(h + off_pairs(c), c->hp.data(), c->hp.size() * sizeof(PairDev));
@@ -425,6 +481,8 @@ FrameDev make_frame_dev(const curast_ctx *c) {
     f.meshes = c->d_meshes.p;
     f.q1 = c->d_q1.p;
     f.q2 = c->d_q2.p;
+    f.rounds = reinterpret_cast<const RoundDev *>(c->d_tab.p + kRoundsOff);
+    f.bits = c->d_bits.p;
     f.ctr = c->d_ctr;
     f.err = c->d_err;
     f.q1_cap = c->cfg.queue1_capacity;
@@ -438,7 +496,7 @@ FrameDev make_frame_dev(const curast_ctx *c) {
     return f;
 }
 
-// clear (optional) -> reset counters -> stage 1 -> stage 2 -> stage 3
+// clear (optional) -> reset counters -> stage 1 (cull, exact) -> stage 2 -> stage 3
 curast_status enqueue_stages(curast_ctx *c, bool clear, bool timing, cudaStream_t s) {
     const FrameDev f = make_frame_dev(c);
     const int sms = c->shape.num_sms;
@@ -447,12 +505,19 @@ curast_status enqueue_stages(curast_ctx *c, bool clear, bool timing, cudaStream_
         for (const ViewDev &v : c->hv) CU(launch_clear(v.vis, (uint64_t)v.W * (uint64_t)v.H, s));
     CU(cudaMemsetAsync(c->d_ctr, 0, sizeof(Counters), s));
     if (timing) CU(cudaEventRecord(c->ev[1], s));
-    CU(launch_stage1(f, c->instanced, sms * c->shape.stage1_blocks_per_sm[c->instanced ? 1 : 0], s));
-    if (timing) CU(cudaEventRecord(c->ev[2], s));
-    CU(launch_stage2(f, sms * c->shape.stage2_blocks_per_sm, s));
+    // stage 1 round by round: the cull fills the survivor bitmap, the exact
+    // kernel empties it (ev[2] falls after the last round's cull)
+    const uint32_t nr = (uint32_t)c->rounds.size();
+    for (uint32_t r = 0; r < nr; ++r) {
+        CU(launch_stage1(f, c->instanced, false, r, sms * c->shape.stage1_blocks_per_sm[c->instanced ? 1 : 0][0], s));
+        if (timing && r + 1 == nr) CU(cudaEventRecord(c->ev[2], s));
+        CU(launch_stage1_exact(f, r, sms * c->shape.stage1x_blocks_per_sm, s));
+    }
     if (timing) CU(cudaEventRecord(c->ev[3], s));
-    CU(launch_stage3(f, sms * c->shape.stage3_blocks_per_sm, s));
+    CU(launch_stage2(f, sms * c->shape.stage2_blocks_per_sm, s));
     if (timing) CU(cudaEventRecord(c->ev[4], s));
+    CU(launch_stage3(f, sms * c->shape.stage3_blocks_per_sm, s));
+    if (timing) CU(cudaEventRecord(c->ev[5], s));
     c->ev_recorded = c->ev_recorded || timing;
     return CURAST_OK;
 }
@@ -468,7 +533,8 @@ curast_status render_views(curast_ctx *c, const curast_view *views, int nv, long
     if (st != CURAST_OK) return st;
     if (!graph) return enqueue_stages(c, clear, true, s);
     std::vector<uint64_t> key = {(uint64_t)nv, (uint64_t)c->instanced, (uint64_t)clear,
-                                 (uint64_t)(uintptr_t)c->d_tab.p, (uint64_t)(uintptr_t)c->d_meshes.p};
+                                 (uint64_t)(uintptr_t)c->d_tab.p, (uint64_t)(uintptr_t)c->d_meshes.p,
+                                 (uint64_t)(uintptr_t)c->d_bits.p, (uint64_t)c->rounds.size()};
     for (int v = 0; v < nv; ++v) {
         key.push_back((uint64_t)views[v].W);
         key.push_back((uint64_t)views[v].H);
@@ -563,7 +629,8 @@ bool valid_config(const curast_config &c) {
     return c.stage1_max_pixels >= 1 && c.stage1_max_pixels <= 1024 && c.stage2_max_pixels >= 32 &&
            c.tile_log2 >= 4 && c.tile_log2 <= 7 && c.stage1_tri_per_thread >= 1 && c.stage1_tri_per_thread <= 4 &&
            c.pairs_per_segment >= 1 && c.pairs_per_segment <= 64 && c.queue1_capacity >= 1 &&
-           c.queue2_capacity >= 1 && c.queue1_capacity <= (1ull << 32) && c.queue2_capacity <= (1ull << 32);
+           c.queue2_capacity >= 1 && c.queue1_capacity <= (1ull << 32) && c.queue2_capacity <= (1ull << 32) &&
+           c.stage1_bitmap_bytes >= (1ull << 12) && c.stage1_bitmap_bytes <= (1ull << 36);
 }
 
 }  // namespace
@@ -602,7 +669,7 @@ curast_status curast_create(curast_ctx **out, int device) {
     curast_status st = CURAST_OK;
     cudaError_t e = query_launch_shape(&c->shape, device);
     if (e != cudaSuccess) st = cuda_status(e);
-    if (st == CURAST_OK && c->shape.stage1_blocks_per_sm[0] < 1) st = CURAST_ERR_NOT_BUILT;
+    if (st == CURAST_OK && c->shape.stage1_blocks_per_sm[0][0] < 1) st = CURAST_ERR_NOT_BUILT;
     if (st == CURAST_OK) st = cuda_status(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
     if (st == CURAST_OK) st = cuda_status(cudaMalloc(reinterpret_cast<void **>(&c->d_ctr), sizeof(Counters)));
     if (st == CURAST_OK) st = cuda_status(cudaMalloc(reinterpret_cast<void **>(&c->d_err), sizeof(unsigned)));
@@ -610,7 +677,7 @@ curast_status curast_create(curast_ctx **out, int device) {
     if (st == CURAST_OK) st = cuda_status(cudaMemset(c->d_ctr, 0, sizeof(Counters)));
     if (st == CURAST_OK) st = cuda_status(cudaMalloc(reinterpret_cast<void **>(&c->d_aabb), (256 * 6 + 6) * sizeof(float)));
     if (st == CURAST_OK) st = cuda_status(cudaMalloc(reinterpret_cast<void **>(&c->d_diff), sizeof(unsigned long long)));
-    for (int k = 0; k < 5 && st == CURAST_OK; ++k) st = cuda_status(cudaEventCreate(&c->ev[k]));
+    for (int k = 0; k < 6 && st == CURAST_OK; ++k) st = cuda_status(cudaEventCreate(&c->ev[k]));
     if (st == CURAST_OK) st = cuda_status(cudaEventCreateWithFlags(&c->ev_tab, cudaEventDisableTiming));
     if (st == CURAST_OK) st = cuda_status(cudaEventCreateWithFlags(&c->ev_inst_mv, cudaEventDisableTiming));
     if (st == CURAST_OK) st = alloc_queues(c);
@@ -637,6 +704,7 @@ void curast_destroy(curast_ctx *c) {
     c->h_tab.release();
     c->d_q1.release();
     c->d_q2.release();
+    c->d_bits.release();
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_aabb) cudaFree(c->d_aabb);
@@ -853,6 +921,7 @@ curast_status curast_last_frame(const curast_ctx *c, curast_frame_info *out) {
     out->pairs = c->hp.size();
     out->segments = c->hs.size();
     out->work_items = c->hdr.n_batches;
+    out->rounds = c->rounds.size();
     std::vector<char> seen(c->meshes.size(), 0);
     for (const PairDev &p : c->hp) {
         out->triangles += c->meshes[p.mesh].T;
@@ -865,12 +934,12 @@ curast_status curast_last_frame(const curast_ctx *c, curast_frame_info *out) {
     return CURAST_OK;
 }
 
-curast_status curast_stage_times(curast_ctx *c, float out[4]) {
+curast_status curast_stage_times(curast_ctx *c, float out[5]) {
     if (!c || !out) return CURAST_ERR_INVALID_ARG;
     if (!c->ev_recorded) return CURAST_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
-    CU(cudaEventSynchronize(c->ev[4]));
-    for (int k = 0; k < 4; ++k) CU(cudaEventElapsedTime(&out[k], c->ev[k], c->ev[k + 1]));
+    CU(cudaEventSynchronize(c->ev[5]));
+    for (int k = 0; k < 5; ++k) CU(cudaEventElapsedTime(&out[k], c->ev[k], c->ev[k + 1]));
     return CURAST_OK;
 }
 

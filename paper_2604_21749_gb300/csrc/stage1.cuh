@@ -61,18 +61,18 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // --------------------------------------------- conservative tiny cull --
 // Per (instance, view) constants of the fast test, staged in shared memory:
-// rows giving X*w, Y*w (pixels) and w by FMA, the error bound
-// margin = ka * max(1/w) + kd, the depth wsafe every vertex must exceed and
-// the window of +-4 screen widths the test is valid in.
+// rows giving X'*w, Y'*w and w by FMA (X' = X - 1/2, so pixel centres sit on
+// integers), the error bound margin = max(1/w) (ka + kb a) + kc a + kd with
+// a the largest |X'|, |Y'| of the triangle, and the region the bound holds in.
 struct __align__(16) FastPair {
     float4 rx, ry, rw;          // (fn[4r], fn[4r+1], fn[4r+2], fn[4r+3])
-    float4 k;                   // ka, kd, wsafe, fast (0 or 1)
-    float4 lim;                 // xlo, xhi, ylo, yhi
-    float wmax, hmax;           // last pixel centre W - 1/2, H - 1/2
-    int pad0, pad1;
+    float4 k;                   // ka, kb, kc, kd
+    float4 lim;                 // wsafe, winx, winy (every w > wsafe, |X'| < winx, |Y'| < winy)
+    float2 last;                // W - 1, H - 1: the last pixel centre
+    float2 pad;
 };
 
-struct Tri9 { float v[9]; };    // the three vertices of a triangle, passed by value
+struct Tri9 { float v[9]; };    // the three vertices of a triangle
 
 // The "bbox holds no pixel centre" test of Section 4.1, done before the
 // exact arithmetic: the estimated bbox widened by the error bound must hold
@@ -97,22 +97,26 @@ __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
         wmn = fminf(wmn, w); rmx = fmaxf(rmx, r);
     }
     const float4 k = fp.k, lim = fp.lim;
-    const float m = __fmaf_rn(k.x, rmx, k.y);
-    const float xl = xmn - m, xh = xmx + m, yl = ymn - m, yh = ymx + m;
-    const bool safe = (wmn > k.z) & (xl > lim.x) & (xh < lim.y) & (yl > lim.z) & (yh < lim.w) & (k.w != 0.0f);
-    // no pixel centre i + 1/2 (0 <= i < W) in [lo, hi]: floor(hi - 1/2) < lo - 1/2,
-    // or the interval ends before the first centre / starts after the last
-    // (exact subtractions: inside the window |lo|, |hi| < 2^22)
-    const bool nx = (floorf(xh - 0.5f) < xl - 0.5f) | (xh < 0.5f) | (xl > fp.wmax);
-    const bool ny = (floorf(yh - 0.5f) < yl - 0.5f) | (yh < 0.5f) | (yl > fp.hmax);
+    const float2 last = fp.last;
+    const float a = fmaxf(fmaxf(fabsf(xmn), fabsf(xmx)), fmaxf(fabsf(ymn), fabsf(ymx)));
+    const float m = __fmaf_rn(rmx, __fmaf_rn(k.y, a, k.x), __fmaf_rn(k.z, a, k.w));
+    const bool safe = (wmn > lim.x) & (xmn > -lim.y) & (xmx < lim.y) & (ymn > -lim.z) & (ymx < lim.z) & (m < 0.5f);
+    // no integer in [lo, hi] within [0, last] on one axis: floor(min(hi, last)) < max(lo, 0)
+    const bool nx = floorf(fminf(xmx + m, last.x)) < fmaxf(xmn - m, 0.0f);
+    const bool ny = floorf(fminf(ymx + m, last.y)) < fmaxf(ymn - m, 0.0f);
     return safe & (nx | ny);
 }
 
-// The exact path of one triangle for one (instance, view): FP32 transform in
-// the fixed order, clip outcodes, snap, culls, then stage-1 raster or queue 1.
-__device__ __noinline__ void exact_triangle(FrameDev f, MeshDev mesh, uint32_t pidx, uint64_t t, Tri9 p,
-                                            bool live) {
+// The exact path of one (triangle, pair) that the conservative cull kept:
+// indices and positions from global memory, FP32 transform in the fixed
+// order, clip outcodes, snap, culls, then stage-1 raster or queue 1.
+// e = (triangle within its mesh, pair).  f must live in parameter or global
+// memory (queue-1 overflow passes its address on).
+__device__ __forceinline__ void exact_body(const FrameDev &f, uint2 e, bool live) {
+    const uint32_t pidx = live ? e.y : 0u;
+    const uint64_t t = live ? e.x : 0u;
     const PairDev &pr = f.pairs[pidx];
+    const MeshDev *mesh = f.meshes + pr.mesh;
     const ViewDev vw = f.views[pr.view];
     Rec r[3];
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
@@ -123,13 +127,17 @@ __device__ __noinline__ void exact_triangle(FrameDev f, MeshDev mesh, uint32_t p
         float mv[12];
 #pragma unroll
         for (int q = 0; q < 12; ++q) mv[q] = pr.mv[q];
+        const uint32_t *ix = mesh->idx + 3 * t;
+        const float *pos = mesh->pos;
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            r[k] = make_rec(to_clip(mv, p.v[3 * k], p.v[3 * k + 1], p.v[3 * k + 2], vw.fx, vw.fy), vw);
+        for (int k = 0; k < 3; ++k) {
+            const float *q = pos + 3 * (uint64_t)__ldg(ix + k);
+            r[k] = make_rec(to_clip(mv, __ldg(q), __ldg(q + 1), __ldg(q + 2), vw.fx, vw.fy), vw);
+        }
         cls = classify(f, r, vw, x0, x1, y0, y1, A, st);
     }
     const uint64_t id = pr.base + t;
-    q1_append(f, cls == kQueue, id, pidx, mesh, t, vw);
+    q1_append(f, cls == kQueue, id, pidx, mesh, t);
     if (cls == kSmall) {
         const int X[3] = {r[0].X, r[1].X, r[2].X}, Y[3] = {r[0].Y, r[1].Y, r[2].Y};
         const float iz[3] = {r[0].iz, r[1].iz, r[2].iz};
@@ -142,6 +150,10 @@ __device__ __noinline__ void exact_triangle(FrameDev f, MeshDev mesh, uint32_t p
     }
 }
 
+// Out-of-line copy for the fused cull kernel (no survivor bitmap), which
+// runs the exact path itself.
+__device__ __noinline__ void exact_survivor(const FrameDev *f, uint2 e, bool live) { exact_body(*f, e, live); }
+
 // ----------------------------------------------------------- the kernel --
 namespace s1 {
 constexpr int kConsumerWarps = 8;
@@ -150,37 +162,39 @@ constexpr int kThreads = kConsumers + 32;            // + one producer warp
 constexpr int kMaxTpt = 4;                           // triangles per consumer per item
 constexpr int kItem = kConsumers * kMaxTpt;          // 1024 triangles, 12 KB of index triples
 constexpr int kSlots = 3;
-constexpr int kQueue = 64;                           // per-warp survivors of the fast cull
+constexpr int kQueue = 64;                           // per-warp survivors (fused kernel)
 constexpr int kMaxPairs = 64;                        // pairs of one segment (pairs_per_segment <= 64)
 
 struct Desc {
-    unsigned long long b;  // work item, >= n_batches: none (consumers stop)
+    unsigned long long b;  // work item, >= the round's end: none (consumers stop)
     uint64_t t0;           // first triangle of the item within its mesh
+    uint64_t wbase;        // bitmap word of (item, pair 0, group 0), relative to the round
     uint32_t n;            // triangles in the item
     uint32_t mesh, pair0, npairs;
 };
 
-template <bool INST>
+template <bool INST, bool FUSED>
 struct Smem {
     uint32_t idx[kSlots][3 * kItem];
     FastPair fp[kSlots][INST ? kMaxPairs : 1];
     MeshDev mesh[kSlots];
     Desc desc[kSlots];
     uint64_t full[kSlots], empty[kSlots];
-    uint4 wq[kConsumerWarps][kQueue];                // (triangle lo, hi, pair, mesh)
+    uint2 wq[FUSED ? kConsumerWarps : 1][FUSED ? kQueue : 1];   // (triangle, pair) survivors
 };
 }  // namespace s1
 
-template <bool INST>
-size_t stage1_smem_bytes() { return sizeof(s1::Smem<INST>); }
+template <bool INST, bool FUSED>
+size_t stage1_smem_bytes() { return sizeof(s1::Smem<INST, FUSED>); }
 
 // Producer warp: work grabs (Section 4.1 "Looping Through Batches": a
 // global counter hands out items until all triangles are done; the counter
 // is read one grab ahead), the forward search for the item's segment, the
-// item's pair constants, and the TMA copy of its index triples.
-template <bool INST>
-__device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST> &S, uint64_t n_batches,
-                                                int n_segs, uint64_t per_item) {
+// item's pair constants, and the TMA copy of its index triples.  Items
+// [rd.b0, rd.b1) form round r of the frame.
+template <bool INST, bool FUSED>
+__device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST, FUSED> &S, const RoundDev &rd,
+                                                uint32_t r, int n_segs, uint64_t per_item, uint32_t G) {
     using namespace s1;
     const int lane = threadIdx.x & 31;
     unsigned long long next = 0;
@@ -188,7 +202,7 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
     unsigned long long seg_end = 0;
     SegDev seg{};
     bool have = false;
-    if (lane == 0) next = atomicAdd(&f.ctr->work, 1ull);
+    if (lane == 0) next = rd.b0 + atomicAdd(&f.ctr->work[r], 1ull);
     for (int j = 0;; ++j) {
         const int slot = j % kSlots;
         if (j >= kSlots && !mbar_wait(&S.empty[slot], ((j / kSlots) - 1) & 1u)) {
@@ -199,8 +213,8 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
         if (lane == 0) {
             const unsigned long long b = next;
             d.b = b;
-            if (b < n_batches) {
-                next = atomicAdd(&f.ctr->work, 1ull);
+            if (b < rd.b1) {
+                next = rd.b0 + atomicAdd(&f.ctr->work[r], 1ull);
                 if (!have || b >= seg_end) {          // galloping forward search: grabs only grow
                     int lo = segidx, step = 1, hi;
                     while (true) {
@@ -219,17 +233,19 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
                     seg_end = lo + 1 < n_segs ? f.segs[lo + 1].batch0 : ~0ull;
                     have = true;
                 }
-                d.t0 = (b - seg.batch0) * per_item;
+                const uint64_t jb = b - seg.batch0;
+                d.t0 = jb * per_item;
                 const uint64_t left = seg.T - d.t0;
                 d.n = (uint32_t)(left < per_item ? left : per_item);
                 d.mesh = seg.mesh;
                 d.pair0 = seg.pair0;
                 d.npairs = INST ? seg.npairs : 1u;
+                d.wbase = seg.word0 + jb * seg.npairs * G - rd.w0;
             }
             S.desc[slot] = d;
         }
         d.b = __shfl_sync(0xffffffffu, d.b, 0);
-        if (d.b >= n_batches) {                       // tell the consumers to stop
+        if (d.b >= rd.b1) {                           // tell the consumers to stop
             __syncwarp();
             mbar_arrive(&S.full[slot]);
             return;
@@ -248,11 +264,10 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
             fp.rx = make_float4(pr.fn[0], pr.fn[1], pr.fn[2], pr.fn[3]);
             fp.ry = make_float4(pr.fn[4], pr.fn[5], pr.fn[6], pr.fn[7]);
             fp.rw = make_float4(pr.fn[8], pr.fn[9], pr.fn[10], pr.fn[11]);
-            fp.k = make_float4(pr.ka, pr.kd, pr.wsafe, pr.fast ? 1.0f : 0.0f);
-            fp.lim = make_float4(-3.0f * vw.hw, 5.0f * vw.hw, -3.0f * vw.hh, 5.0f * vw.hh);
-            fp.wmax = (float)vw.W - 0.5f;
-            fp.hmax = (float)vw.H - 0.5f;
-            fp.pad0 = fp.pad1 = 0;
+            fp.k = make_float4(pr.fk[0], pr.fk[1], pr.fk[2], pr.fk[3]);
+            fp.lim = make_float4(pr.wsafe, pr.winx, pr.winy, 0.0f);
+            fp.last = make_float2((float)(vw.W - 1), (float)(vw.H - 1));
+            fp.pad = make_float2(0.0f, 0.0f);
             S.fp[slot][q] = fp;
         }
         const uint32_t bytes = 12u * d.n;
@@ -271,23 +286,28 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
     }
 }
 
-// Persistent stage-1 kernel.  Consumers take one triangle at a time: three
-// index words from shared memory, nine position floats from global memory,
-// then for every pair of the item the conservative tiny-triangle cull.
-// Triangles it keeps are queued per warp and run through the exact path 32
-// at a time, so that path never runs with idle lanes.  INST blocks loop over
-// many pairs (Section 4.5, extended to several views): a triangle's data is
-// loaded once for all of them.
-template <bool INST>
-__global__ void __launch_bounds__(s1::kThreads, 3) k_stage1(FrameDev f) {
+// Persistent stage-1 cull kernel, round r of the frame.  Consumers take one
+// triangle at a time: three index words from shared memory, nine position
+// floats from global memory, then for every pair of the item the
+// conservative tiny-triangle cull.  The warp's ballot of the triangles it
+// keeps is stored as one word of the survivor bitmap (32 consecutive
+// triangles of one pair), which k_stage1_exact works through afterwards;
+// the cull stays free of the exact path's registers.  The FUSED form (no
+// bitmap) queues the survivors per warp and runs the exact path itself,
+// 32 at a time.  INST blocks loop over many pairs (Section 4.5, extended to
+// several views): a triangle's data is loaded once for all of them.
+template <bool INST, bool FUSED>
+__global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : 4)
+    k_stage1(const __grid_constant__ FrameDev f, uint32_t r) {
     using namespace s1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem<INST> &S = *reinterpret_cast<Smem<INST> *>(smem_raw);
+    Smem<INST, FUSED> &S = *reinterpret_cast<Smem<INST, FUSED> *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint64_t n_batches = f.hdr->n_batches;
+    const RoundDev rd = f.rounds[r];
     const int n_segs = (int)f.hdr->n_segs;
     const uint32_t tpt = f.tpt;
     const uint64_t per_item = (uint64_t)kConsumers * tpt;
+    const uint32_t G = kConsumerWarps * tpt;          // 32-triangle groups per item
 
     if (tid == 0) {
         for (int s = 0; s < kSlots; ++s) {
@@ -299,32 +319,13 @@ __global__ void __launch_bounds__(s1::kThreads, 3) k_stage1(FrameDev f) {
     __syncthreads();
 
     if (warp == kConsumerWarps) {
-        stage1_producer<INST>(f, S, n_batches, n_segs, per_item);
+        stage1_producer<INST, FUSED>(f, S, rd, r, n_segs, per_item, G);
         return;
     }
 
-    // Survivors of the fast cull are queued per warp as (triangle, pair,
-    // mesh) and run through the exact path 32 at a time, so that path never
-    // runs with idle lanes.  The queue outlives the items (entries name the
-    // triangle globally) and is emptied only when full and at the end.
-    uint4 *wq = S.wq[warp];
+    uint2 *wq = S.wq[FUSED ? warp : 0];
     const unsigned lt_mask = (1u << lane) - 1u;
     int qn = 0;
-    auto run_exact = [&](uint4 e, bool has) {
-        const MeshDev mesh = f.meshes[has ? e.w : 0u];
-        const uint64_t t = has ? ((uint64_t)e.y << 32 | e.x) : 0;
-        Tri9 p;
-#pragma unroll
-        for (int c = 0; c < 9; ++c) p.v[c] = 0.0f;
-        if (has) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float *q = mesh.pos + 3 * (uint64_t)__ldg(mesh.idx + 3 * t + c);
-                p.v[3 * c] = __ldg(q); p.v[3 * c + 1] = __ldg(q + 1); p.v[3 * c + 2] = __ldg(q + 2);
-            }
-        }
-        exact_triangle(f, mesh, has ? e.z : 0u, t, p, has);
-    };
     for (int j = 0;; ++j) {
         const int slot = j % kSlots;
         if (!mbar_wait(&S.full[slot], (j / kSlots) & 1u)) {
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(s1::kThreads, 3) k_stage1(FrameDev f) {
             return;
         }
         const Desc d = S.desc[slot];
-        if (d.b >= n_batches) break;
+        if (d.b >= rd.b1) break;
         const MeshDev mesh = S.mesh[slot];
         const uint32_t *idx = S.idx[slot];
         const uint32_t np = INST ? d.npairs : 1u;
@@ -360,22 +361,20 @@ __global__ void __launch_bounds__(s1::kThreads, 3) k_stage1(FrameDev f) {
 #pragma unroll
                 for (int c = 0; c < 9; ++c) p.v[c] = 0.0f;
             }
-            const uint64_t t = d.t0 + lt;
             for (uint32_t pi = 0; pi < np; ++pi) {
                 const bool live = valid && !fast_cull(S.fp[slot][pi], p);
-                if (f.stats && valid) {
-                    if (live) stat_add(f, kStatFast, 1);
-                    else stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
-                }
+                if (f.stats && valid && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
                 const unsigned m = __ballot_sync(0xffffffffu, live);
-                if (m) {
-                    if (live)
-                        wq[qn + __popc(m & lt_mask)] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), d.pair0 + pi, d.mesh);
+                if (!FUSED) {
+                    if (lane == 0) f.bits[d.wbase + pi * G + k * kConsumerWarps + warp] = m;
+                } else if (m) {
+                    if (f.stats && live) stat_add(f, kStatFast, 1);
+                    if (live) wq[qn + __popc(m & lt_mask)] = make_uint2((uint32_t)(d.t0 + lt), d.pair0 + pi);
                     qn += __popc(m);
                     __syncwarp();
                     if (qn >= 32) {
                         qn -= 32;
-                        run_exact(wq[qn + lane], true);
+                        exact_survivor(&f, wq[qn + lane], true);
                         __syncwarp();
                     }
                 }
@@ -385,5 +384,66 @@ __global__ void __launch_bounds__(s1::kThreads, 3) k_stage1(FrameDev f) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[slot]);
     }
-    if (qn > 0) run_exact(wq[lane < (unsigned)qn ? lane : 0], lane < (unsigned)qn);
+    if (FUSED && qn > 0) exact_survivor(&f, wq[lane < qn ? lane : 0], lane < qn);
+}
+
+// Stage 1, exact part of round r: the survivor bitmap of the cull, 32 words
+// per warp.  Each lane decodes its word to (first triangle, pair), the warp
+// compacts the set bits into shared memory and then runs the exact path on
+// 32 survivors at a time.
+namespace s1 {
+constexpr int kExactWarps = 4;
+}
+__global__ void __launch_bounds__(32 * s1::kExactWarps) k_stage1_exact(const __grid_constant__ FrameDev f, uint32_t r) {
+    using namespace s1;
+    __shared__ uint2 buf[kExactWarps][32 * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RoundDev rd = f.rounds[r];
+    const uint64_t nwords = rd.w1 - rd.w0;
+    const int n_segs = (int)f.hdr->n_segs;
+    const uint32_t G = kConsumerWarps * f.tpt;
+    const uint64_t per_item = (uint64_t)kConsumers * f.tpt;
+    const uint64_t nw = (uint64_t)gridDim.x * kExactWarps;
+    for (uint64_t c = (uint64_t)blockIdx.x * kExactWarps + warp; 32 * c < nwords; c += nw) {
+        const uint64_t p = 32 * c + lane;
+        uint32_t m = p < nwords ? __ldcs(f.bits + p) : 0u;
+        uint64_t t0 = 0;
+        uint32_t pair = 0;
+        if (m) {
+            // the segment holding global word gw: the last one with word0 <= gw
+            const uint64_t gw = rd.w0 + p;
+            int lo = 0, hi = n_segs;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (f.segs[mid].word0 <= gw) lo = mid; else hi = mid;
+            }
+            const SegDev &sg = f.segs[lo];
+            const uint64_t local = gw - sg.word0;
+            const uint32_t per = sg.npairs * G;                 // words per item (<= 64 * 32)
+            const uint64_t jb = local < (1ull << 32) ? (uint64_t)((uint32_t)local / per) : local / per;
+            const uint32_t rem = (uint32_t)(local - jb * per);
+            const uint32_t pi = rem / G, g = rem - pi * G;
+            t0 = jb * per_item + 32ull * g;
+            pair = sg.pair0 + pi;
+        }
+        const int cnt = __popc(m);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) continue;
+        if (f.stats && lane == 0) stat_add(f, kStatFast, (unsigned long long)total);
+        int at = incl - cnt;
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1u;
+            buf[warp][at++] = make_uint2((uint32_t)(t0 + (uint64_t)bit), pair);
+        }
+        __syncwarp();
+        for (int i = lane; i < total; i += 32) exact_body(f, buf[warp][i], true);
+        __syncwarp();
+    }
 }

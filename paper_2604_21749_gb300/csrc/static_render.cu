@@ -28,7 +28,8 @@ constexpr size_t kOffHdr = 0;
 constexpr size_t kOffView = al(kOffHdr + sizeof(FrameHdr));
 constexpr size_t kOffMesh = al(kOffView + sizeof(ViewDev));
 constexpr size_t kOffSeg = al(kOffMesh + sizeof(MeshDev));
-constexpr size_t kOffCtr = al(kOffSeg + sizeof(SegDev));
+constexpr size_t kOffRound = al(kOffSeg + sizeof(SegDev));
+constexpr size_t kOffCtr = al(kOffRound + sizeof(RoundDev));
 constexpr size_t kOffErr = al(kOffCtr + sizeof(Counters));
 constexpr size_t kOffPairs = al(kOffErr + sizeof(unsigned));
 constexpr size_t kOffQ1 = al(kOffPairs + kStaticMaxInstances * sizeof(PairDev));
@@ -45,6 +46,7 @@ struct StaticFrame {
     ViewDev view;
     MeshDev mesh;
     SegDev seg;
+    RoundDev round;
     int n;
     float mv[kStaticMaxInstances][12];
     uint64_t base[kStaticMaxInstances];
@@ -59,8 +61,9 @@ __global__ void k_static_setup(StaticFrame s) {
         PairDev p;
         for (int q = 0; q < 12; ++q) p.mv[q] = s.mv[t][q];
         for (int q = 0; q < 12; ++q) p.fn[q] = 0.0f;
-        p.ka = p.kd = p.wsafe = 0.0f;
-        p.fast = 0;   // no conservative cull: every triangle takes the exact path
+        for (int q = 0; q < 4; ++q) p.fk[q] = 0.0f;
+        p.wsafe = INFINITY;   // no conservative cull: every triangle takes the exact path
+        p.winx = p.winy = 0.0f;
         p.base = s.base[t];
         p.view = 0;
         p.mesh = 0;
@@ -71,6 +74,7 @@ __global__ void k_static_setup(StaticFrame s) {
         *reinterpret_cast<ViewDev *>(g + kOffView) = s.view;
         *reinterpret_cast<MeshDev *>(g + kOffMesh) = s.mesh;
         *reinterpret_cast<SegDev *>(g + kOffSeg) = s.seg;
+        *reinterpret_cast<RoundDev *>(g + kOffRound) = s.round;
         *reinterpret_cast<unsigned *>(g + kOffErr) = 0u;
     }
     unsigned long long *c = reinterpret_cast<unsigned long long *>(g + kOffCtr);
@@ -157,6 +161,9 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     fr.hdr.n_batches = T ? (T + per_item - 1) / per_item : 0;
     fr.hdr.n_segs = T ? 1u : 0u;
     fr.hdr.n_views = 1;
+    fr.hdr.n_rounds = 1;
+    fr.round.b0 = 0;                      // one round over every item; no bitmap (fused stage 1)
+    fr.round.b1 = fr.hdr.n_batches;
     fr.view.fx = proj[0];
     fr.view.fy = proj[5];
     fr.view.nearv = nearv;
@@ -184,6 +191,8 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     f.meshes = reinterpret_cast<const MeshDev *>(g + kOffMesh);
     f.q1 = reinterpret_cast<Q1Entry *>(g + kOffQ1);
     f.q2 = reinterpret_cast<Q2Entry *>(g + kOffQ2);
+    f.rounds = reinterpret_cast<const RoundDev *>(g + kOffRound);
+    f.bits = nullptr;   // no survivor bitmap: the fused cull kernel runs the exact path itself
     f.ctr = reinterpret_cast<Counters *>(g + kOffCtr);
     f.err = reinterpret_cast<unsigned *>(g + kOffErr);
     f.q1_cap = kStaticQ1;
@@ -200,7 +209,7 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     k_static_setup<<<1, 32, 0, s>>>(fr);
     if ((e = cudaGetLastError()) != cudaSuccess) return CURAST_ERR_CUDA;
     if ((e = launch_clear(vis, (uint64_t)W * (uint64_t)H, s)) != cudaSuccess) return CURAST_ERR_CUDA;
-    if ((e = launch_stage1(f, inst, sms * ds->shape.stage1_blocks_per_sm[inst ? 1 : 0], s)) != cudaSuccess)
+    if ((e = launch_stage1(f, inst, true, 0, sms * ds->shape.stage1_blocks_per_sm[inst ? 1 : 0][1], s)) != cudaSuccess)
         return CURAST_ERR_CUDA;
     if ((e = launch_stage2(f, sms * ds->shape.stage2_blocks_per_sm, s)) != cudaSuccess) return CURAST_ERR_CUDA;
     if ((e = launch_stage3(f, sms * ds->shape.stage3_blocks_per_sm, s)) != cudaSuccess) return CURAST_ERR_CUDA;

@@ -60,6 +60,7 @@ def test_small_workload_bit_exact_and_resolve(api, small):
     dict(stage2_max_pixels=1 << 30), dict(tile_log2=4), dict(tile_log2=7),
     dict(stage1_tri_per_thread=1), dict(stage1_tri_per_thread=3),
     dict(queue1_capacity=1, queue2_capacity=1), dict(queue1_capacity=7, queue2_capacity=3),
+    dict(stage1_bitmap_bytes=1 << 12), dict(stage1_bitmap_bytes=1 << 12, stage1_tri_per_thread=1),
 ])
 def test_stage_choices_never_change_visibility(api, small, cfg):
     """Thresholds, tile size, batch shape and queue overflow move triangles
@@ -72,6 +73,8 @@ def test_stage_choices_never_change_visibility(api, small, cfg):
     assert_vis_equal(vis, oracle_vis(small, cam), str(cfg))
     if cfg.get("queue1_capacity", 1 << 30) < 2:
         assert st["queue1_overflow"] > 0
+    if cfg.get("stage1_bitmap_bytes", 1 << 30) < 1 << 14:
+        assert r.last_frame()["rounds"] > 1          # stage 1 ran in several cull + exact rounds
     del keep
 
 
@@ -100,11 +103,12 @@ def mixed():
     return _mixed_scene()
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_batched_views_equal_oracle(api, mixed, use_graph):
+@pytest.mark.parametrize("use_graph,bitmap", [(False, 1 << 30), (True, 1 << 30), (True, 1 << 12)])
+def test_batched_views_equal_oracle(api, mixed, use_graph, bitmap):
     """Many meshes, rotated/scaled instances (some culled), an empty mesh and
-    three views of different sizes in one batched launch (graph or not)."""
-    r = _renderer(api, pairs_per_segment=7)
+    three views of different sizes in one batched launch (graph or not; one
+    stage-1 round or several)."""
+    r = _renderer(api, pairs_per_segment=7, stage1_bitmap_bytes=bitmap)
     keep = upload(r, mixed)
     views = [(c.view, c.proj, c.W, c.H, None) for c in mixed.cameras]
     for frame in range(2):   # the second frame replays the captured graph
