@@ -34,10 +34,10 @@ struct PairDev {             // one (instance, view) pair that survived host cul
     // the estimate and the exact snapped position lie at most
     // margin = max(1/w) * (fk0 + fk1 a) + fk2 a + fk3 pixels apart, a the
     // largest |X'|, |Y'| of the triangle, while every w exceeds wsafe and
-    // every |X'| < winx, |Y'| < winy; wsafe = +inf disables the test
+    // every |X'|, |Y'| < win; wsafe = +inf disables the test
     float fn[12];
     float fk[4];
-    float wsafe, winx, winy;
+    float wsafe, win;
     uint64_t base;           // global id of the instance's triangle 0
     uint32_t view;
     uint32_t mesh;

@@ -148,7 +148,7 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     std::memset(p.fn, 0, sizeof(p.fn));
     std::memset(p.fk, 0, sizeof(p.fk));
     p.wsafe = INFINITY;
-    p.winx = p.winy = 0.0f;
+    p.win = 0.0f;
     if (!m.bounded) return;
     // u: FP32 unit roundoff; rho: relative error assumed for rcp.approx.ftz.f32
     // (8x the documented one ulp)
@@ -186,10 +186,10 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     p.fk[2] = (float)(kc * (1 + 1e-6));
     p.fk[3] = (float)(kd * (1 + 1e-6));
     p.wsafe = (float)(ws * (1 + 1e-6));
-    // inside +-4 screen extents every vertex lies far within the guard band
-    // (|X - W/2| <= 128 W/2), so the exact path would not clip it
-    p.winx = (float)(8.0 * hw);
-    p.winy = (float)(8.0 * hh);
+    // inside |X'|, |Y'| < 8 min(W/2, H/2) every vertex lies far within the
+    // guard band (|X - W/2| <= 128 W/2, likewise for Y), so the exact path
+    // would not clip it
+    p.win = (float)(8.0 * std::min(hw, hh));
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

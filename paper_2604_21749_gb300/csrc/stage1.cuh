@@ -67,9 +67,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
 struct __align__(16) FastPair {
     float4 rx, ry, rw;          // (fn[4r], fn[4r+1], fn[4r+2], fn[4r+3])
     float4 k;                   // ka, kb, kc, kd
-    float4 lim;                 // wsafe, winx, winy (every w > wsafe, |X'| < winx, |Y'| < winy)
-    float2 last;                // W - 1, H - 1: the last pixel centre
-    float2 pad;
+    float4 lim;                 // wsafe, win, W - 1, H - 1 (every w > wsafe and |X'|, |Y'| < win;
+                                // the last pixel centre)
 };
 
 struct Tri9 { float v[9]; };    // the three vertices of a triangle
@@ -97,13 +96,12 @@ __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
         wmn = fminf(wmn, w); rmx = fmaxf(rmx, r);
     }
     const float4 k = fp.k, lim = fp.lim;
-    const float2 last = fp.last;
     const float a = fmaxf(fmaxf(fabsf(xmn), fabsf(xmx)), fmaxf(fabsf(ymn), fabsf(ymx)));
     const float m = __fmaf_rn(rmx, __fmaf_rn(k.y, a, k.x), __fmaf_rn(k.z, a, k.w));
-    const bool safe = (wmn > lim.x) & (xmn > -lim.y) & (xmx < lim.y) & (ymn > -lim.z) & (ymx < lim.z) & (m < 0.5f);
+    const bool safe = (wmn > lim.x) & (a < lim.y) & (m < 0.5f);
     // no integer in [lo, hi] within [0, last] on one axis: floor(min(hi, last)) < max(lo, 0)
-    const bool nx = floorf(fminf(xmx + m, last.x)) < fmaxf(xmn - m, 0.0f);
-    const bool ny = floorf(fminf(ymx + m, last.y)) < fmaxf(ymn - m, 0.0f);
+    const bool nx = floorf(fminf(xmx + m, lim.z)) < fmaxf(xmn - m, 0.0f);
+    const bool ny = floorf(fminf(ymx + m, lim.w)) < fmaxf(ymn - m, 0.0f);
     return safe & (nx | ny);
 }
 
@@ -112,7 +110,24 @@ __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
 // order, clip outcodes, snap, culls, then stage-1 raster or queue 1.
 // e = (triangle within its mesh, pair).  f must live in parameter or global
 // memory (queue-1 overflow passes its address on).
-__device__ __forceinline__ void exact_body(const FrameDev &f, uint2 e, bool live) {
+__device__ __forceinline__ void exact_gather(const FrameDev &f, uint2 e, bool live, Tri9 &p) {
+    if (live) {
+        const MeshDev *mesh = f.meshes + f.pairs[e.y].mesh;
+        const uint32_t *ix = mesh->idx + 3 * (uint64_t)e.x;
+        const float *pos = mesh->pos;
+        const uint32_t i0 = __ldg(ix), i1 = __ldg(ix + 1), i2 = __ldg(ix + 2);
+        const float *q0 = pos + 3 * (uint64_t)i0, *q1 = pos + 3 * (uint64_t)i1, *q2 = pos + 3 * (uint64_t)i2;
+        p.v[0] = __ldg(q0); p.v[1] = __ldg(q0 + 1); p.v[2] = __ldg(q0 + 2);
+        p.v[3] = __ldg(q1); p.v[4] = __ldg(q1 + 1); p.v[5] = __ldg(q1 + 2);
+        p.v[6] = __ldg(q2); p.v[7] = __ldg(q2 + 1); p.v[8] = __ldg(q2 + 2);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) p.v[c] = 0.0f;
+    }
+}
+
+// The exact path given the triangle's positions (from exact_gather).
+__device__ __forceinline__ void exact_compute(const FrameDev &f, uint2 e, bool live, const Tri9 &p) {
     const uint32_t pidx = live ? e.y : 0u;
     const uint64_t t = live ? e.x : 0u;
     const PairDev &pr = f.pairs[pidx];
@@ -127,13 +142,9 @@ __device__ __forceinline__ void exact_body(const FrameDev &f, uint2 e, bool live
         float mv[12];
 #pragma unroll
         for (int q = 0; q < 12; ++q) mv[q] = pr.mv[q];
-        const uint32_t *ix = mesh->idx + 3 * t;
-        const float *pos = mesh->pos;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float *q = pos + 3 * (uint64_t)__ldg(ix + k);
-            r[k] = make_rec(to_clip(mv, __ldg(q), __ldg(q + 1), __ldg(q + 2), vw.fx, vw.fy), vw);
-        }
+        for (int k = 0; k < 3; ++k)
+            r[k] = make_rec(to_clip(mv, p.v[3 * k], p.v[3 * k + 1], p.v[3 * k + 2], vw.fx, vw.fy), vw);
         cls = classify(f, r, vw, x0, x1, y0, y1, A, st);
     }
     const uint64_t id = pr.base + t;
@@ -150,6 +161,12 @@ __device__ __forceinline__ void exact_body(const FrameDev &f, uint2 e, bool live
     }
 }
 
+__device__ __forceinline__ void exact_body(const FrameDev &f, uint2 e, bool live) {
+    Tri9 p;
+    exact_gather(f, e, live, p);
+    exact_compute(f, e, live, p);
+}
+
 // Out-of-line copy for the fused cull kernel (no survivor bitmap), which
 // runs the exact path itself.
 __device__ __noinline__ void exact_survivor(const FrameDev *f, uint2 e, bool live) { exact_body(*f, e, live); }
@@ -164,6 +181,8 @@ constexpr int kItem = kConsumers * kMaxTpt;          // 1024 triangles, 12 KB of
 constexpr int kSlots = 3;
 constexpr int kQueue = 64;                           // per-warp survivors (fused kernel)
 constexpr int kMaxPairs = 64;                        // pairs of one segment (pairs_per_segment <= 64)
+constexpr int kNT = 2;                               // triangles a lane loads together (single-pair items)
+constexpr int kCullBlocks = 4;                       // cull blocks per SM: 56 registers a thread
 
 struct Desc {
     unsigned long long b;  // work item, >= the round's end: none (consumers stop)
@@ -265,9 +284,7 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
             fp.ry = make_float4(pr.fn[4], pr.fn[5], pr.fn[6], pr.fn[7]);
             fp.rw = make_float4(pr.fn[8], pr.fn[9], pr.fn[10], pr.fn[11]);
             fp.k = make_float4(pr.fk[0], pr.fk[1], pr.fk[2], pr.fk[3]);
-            fp.lim = make_float4(pr.wsafe, pr.winx, pr.winy, 0.0f);
-            fp.last = make_float2((float)(vw.W - 1), (float)(vw.H - 1));
-            fp.pad = make_float2(0.0f, 0.0f);
+            fp.lim = make_float4(pr.wsafe, pr.win, (float)(vw.W - 1), (float)(vw.H - 1));
             S.fp[slot][q] = fp;
         }
         const uint32_t bytes = 12u * d.n;
@@ -297,7 +314,7 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
 // 32 at a time.  INST blocks loop over many pairs (Section 4.5, extended to
 // several views): a triangle's data is loaded once for all of them.
 template <bool INST, bool FUSED>
-__global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : 4)
+__global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
     k_stage1(const __grid_constant__ FrameDev f, uint32_t r) {
     using namespace s1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -337,6 +354,50 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : 4)
         const MeshDev mesh = S.mesh[slot];
         const uint32_t *idx = S.idx[slot];
         const uint32_t np = INST ? d.npairs : 1u;
+        if (!INST && !FUSED) {
+            // one pair per item: its constants stay in registers for the item;
+            // NT triangles per lane are loaded together (more loads in flight)
+            constexpr int NT = kNT;
+            const FastPair fp = S.fp[slot][0];
+            for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
+                bool valid[NT];
+                uint32_t ix[NT][3];
+#pragma unroll
+                for (int u = 0; u < NT; ++u) {
+                    const uint32_t lt = (k + u) * kConsumers + tid;
+                    valid[u] = k + u < tpt && lt < d.n;
+                    ix[u][0] = ix[u][1] = ix[u][2] = 0;
+                    if (valid[u]) {
+                        ix[u][0] = idx[3 * lt]; ix[u][1] = idx[3 * lt + 1]; ix[u][2] = idx[3 * lt + 2];
+                        if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= mesh.V) {
+                            if (f.check) atomicOr(f.err, kErrIndex);
+                            valid[u] = false;
+                        }
+                    }
+                }
+                Tri9 p[NT];
+#pragma unroll
+                for (int u = 0; u < NT; ++u) {
+                    if (valid[u]) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float *q = mesh.pos + 3 * (uint64_t)ix[u][c];
+                            p[u].v[3 * c] = __ldg(q); p[u].v[3 * c + 1] = __ldg(q + 1); p[u].v[3 * c + 2] = __ldg(q + 2);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < NT; ++u) {
+                    const bool live = valid[u] && !fast_cull(fp, p[u]);
+                    if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
+                    const unsigned m = __ballot_sync(0xffffffffu, live);
+                    if (k + u < tpt && lane == 0) f.bits[d.wbase + (k + u) * kConsumerWarps + warp] = m;
+                }
+            }
+        } else
         for (uint32_t k = 0; k < tpt; ++k) {          // uniform trip count: the warp stays converged
             // three index words from shared memory, nine position floats from
             // global memory; an index >= V skips the triangle (reported when checking)
@@ -387,16 +448,24 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : 4)
     if (FUSED && qn > 0) exact_survivor(&f, wq[lane < qn ? lane : 0], lane < qn);
 }
 
-// Stage 1, exact part of round r: the survivor bitmap of the cull, 32 words
-// per warp.  Each lane decodes its word to (first triangle, pair), the warp
-// compacts the set bits into shared memory and then runs the exact path on
-// 32 survivors at a time.
+// Stage 1, exact part of round r, from the survivor bitmap of the cull.  A
+// warp walks its share of the bitmap 32 words at a time: each lane decodes
+// its word to (first triangle, pair) -- the segment is found by a forward
+// search from the warp's previous one, since a warp's words only grow --
+// and the set bits are compacted into a shared-memory batch of up to
+// 32 * kExactK survivors.  A full batch is gathered at once (every lane
+// issues the index and position loads of its kExactK survivors before any
+// arithmetic) and then run through the exact path.
 namespace s1 {
 constexpr int kExactWarps = 4;
+constexpr int kExactBlocks = 4;                      // 128 registers a thread
+constexpr int kExactK = 2;                           // survivors a lane gathers together
+constexpr int kBatch = 32 * kExactK;
 }
-__global__ void __launch_bounds__(32 * s1::kExactWarps) k_stage1_exact(const __grid_constant__ FrameDev f, uint32_t r) {
+__global__ void __launch_bounds__(32 * s1::kExactWarps, s1::kExactBlocks)
+    k_stage1_exact(const __grid_constant__ FrameDev f, uint32_t r) {
     using namespace s1;
-    __shared__ uint2 buf[kExactWarps][32 * 32];
+    __shared__ uint2 buf[kExactWarps][kBatch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RoundDev rd = f.rounds[r];
     const uint64_t nwords = rd.w1 - rd.w0;
@@ -404,46 +473,74 @@ __global__ void __launch_bounds__(32 * s1::kExactWarps) k_stage1_exact(const __g
     const uint32_t G = kConsumerWarps * f.tpt;
     const uint64_t per_item = (uint64_t)kConsumers * f.tpt;
     const uint64_t nw = (uint64_t)gridDim.x * kExactWarps;
-    for (uint64_t c = (uint64_t)blockIdx.x * kExactWarps + warp; 32 * c < nwords; c += nw) {
-        const uint64_t p = 32 * c + lane;
-        uint32_t m = p < nwords ? __ldcs(f.bits + p) : 0u;
-        uint64_t t0 = 0;
-        uint32_t pair = 0;
-        if (m) {
-            // the segment holding global word gw: the last one with word0 <= gw
-            const uint64_t gw = rd.w0 + p;
-            int lo = 0, hi = n_segs;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (f.segs[mid].word0 <= gw) lo = mid; else hi = mid;
+    uint64_t c = (uint64_t)blockIdx.x * kExactWarps + warp;   // the next chunk of 32 words
+    uint32_t m_next = 32 * c + lane < nwords ? __ldcs(f.bits + 32 * c + lane) : 0u;
+    uint32_t m = 0;                                 // bits of the lane's word not yet batched
+    uint64_t t0 = 0;
+    uint32_t pair = 0;
+    int seg = 0;                                    // segment of the warp's last word so far
+    bool more = 32 * c < nwords;
+    while (true) {
+        int n = 0;                                  // survivors in the batch (warp-uniform)
+        while (n < kBatch) {
+            if (__ballot_sync(0xffffffffu, m != 0) == 0) {
+                if (!more) break;
+                m = m_next;                         // advance to chunk c
+                const uint64_t gw = rd.w0 + 32 * c + lane;
+                const uint64_t cn = c + nw;
+                m_next = 32 * cn + lane < nwords ? __ldcs(f.bits + 32 * cn + lane) : 0u;
+                if (__ballot_sync(0xffffffffu, m != 0) != 0) {
+                    int sl = seg;
+                    while (sl + 1 < n_segs && f.segs[sl + 1].word0 <= gw) ++sl;
+                    seg = __shfl_sync(0xffffffffu, sl, 31);
+                    if (m) {
+                        const SegDev &sg = f.segs[sl];
+                        const uint64_t local = gw - sg.word0;
+                        const uint32_t per = sg.npairs * G;         // words per item (<= 64 * 32)
+                        const uint64_t jb = local < (1ull << 32) ? (uint64_t)((uint32_t)local / per) : local / per;
+                        const uint32_t rem = (uint32_t)(local - jb * per);
+                        const uint32_t pi = rem / G, g = rem - pi * G;
+                        t0 = jb * per_item + 32ull * g;
+                        pair = sg.pair0 + pi;
+                    }
+                }
+                c = cn;
+                more = 32 * c < nwords;
+                continue;
             }
-            const SegDev &sg = f.segs[lo];
-            const uint64_t local = gw - sg.word0;
-            const uint32_t per = sg.npairs * G;                 // words per item (<= 64 * 32)
-            const uint64_t jb = local < (1ull << 32) ? (uint64_t)((uint32_t)local / per) : local / per;
-            const uint32_t rem = (uint32_t)(local - jb * per);
-            const uint32_t pi = rem / G, g = rem - pi * G;
-            t0 = jb * per_item + 32ull * g;
-            pair = sg.pair0 + pi;
-        }
-        const int cnt = __popc(m);
-        int incl = cnt;
+            // append the lowest set bits of every lane's word, as many as fit
+            const int cnt = __popc(m);
+            int incl = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            int at = n + incl - cnt;
+            while (m && at < kBatch) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1u;
+                buf[warp][at++] = make_uint2((uint32_t)(t0 + (uint64_t)bit), pair);
+            }
+            n = min(n + total, kBatch);
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0) continue;
-        if (f.stats && lane == 0) stat_add(f, kStatFast, (unsigned long long)total);
-        int at = incl - cnt;
-        while (m) {
-            const int bit = __ffs(m) - 1;
-            m &= m - 1u;
-            buf[warp][at++] = make_uint2((uint32_t)(t0 + (uint64_t)bit), pair);
+        if (n == 0) break;
+        __syncwarp();
+        if (f.stats && lane == 0) stat_add(f, kStatFast, (unsigned long long)n);
+        uint2 e[kExactK];
+        bool live[kExactK];
+        Tri9 p[kExactK];
+#pragma unroll
+        for (int u = 0; u < kExactK; ++u) {
+            live[u] = lane + 32 * u < n;
+            e[u] = buf[warp][live[u] ? lane + 32 * u : 0];
         }
+#pragma unroll
+        for (int u = 0; u < kExactK; ++u) exact_gather(f, e[u], live[u], p[u]);
         __syncwarp();
-        for (int i = lane; i < total; i += 32) exact_body(f, buf[warp][i], true);
-        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kExactK; ++u)
+            if (__any_sync(0xffffffffu, live[u])) exact_compute(f, e[u], live[u], p[u]);
     }
 }

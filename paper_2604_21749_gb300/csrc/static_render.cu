@@ -63,7 +63,7 @@ __global__ void k_static_setup(StaticFrame s) {
         for (int q = 0; q < 12; ++q) p.fn[q] = 0.0f;
         for (int q = 0; q < 4; ++q) p.fk[q] = 0.0f;
         p.wsafe = INFINITY;   // no conservative cull: every triangle takes the exact path
-        p.winx = p.winy = 0.0f;
+        p.win = 0.0f;
         p.base = s.base[t];
         p.view = 0;
         p.mesh = 0;
