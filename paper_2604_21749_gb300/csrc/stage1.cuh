@@ -355,10 +355,11 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
         const uint32_t *idx = S.idx[slot];
         const uint32_t np = INST ? d.npairs : 1u;
         if (!INST && !FUSED) {
-            // one pair per item: its constants stay in registers for the item;
-            // NT triangles per lane are loaded together (more loads in flight)
+            // one pair per item; NT triangles per lane are loaded together (more
+            // loads in flight; the pair constants are read from shared memory,
+            // which leaves the registers to the loads)
             constexpr int NT = kNT;
-            const FastPair fp = S.fp[slot][0];
+            const FastPair &fp = S.fp[slot][0];
             for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
                 bool valid[NT];
                 uint32_t ix[NT][3];
