@@ -171,7 +171,7 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     //   (9.002u a S_axis + 4.001u b S_z + 4.001u h S_z + 7.002u (|X'| + 1) S_z) / w
     //   + (|X'| + 1)(rho + 7.01u) + 5.01u (h + 1) + 1/512 (the snap),
     // with 1/w <= max(1/w~) (1 + 4u S_z / wsafe) / (1 - rho) for the estimated w~.
-    const double ws = v.nearv * (1 + 1e-3) + 8 * u * S[2];
+    double ws = v.nearv * (1 + 1e-3) + 8 * u * S[2];
     const double F = 1.01 * (1 + 4 * u * S[2] / ws) / (1 - rho);
     const double kax = 9.002 * ax * S[0] + 4.001 * bx * S[2] + 4.001 * hw * S[2] + 7.002 * S[2];
     const double kay = 9.002 * ay * S[1] + 4.001 * by * S[2] + 4.001 * hh * S[2] + 7.002 * S[2];
@@ -179,6 +179,13 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     const double kb = F * u * 7.002 * S[2];
     const double kc = 1.01 * (rho + 7.01 * u);
     const double kd = 1.01 * (5.01 * u * (std::max(hw, hh) + 1) + rho + 7.01 * u) + 1.0 / 512;
+    const double win = 8.0 * std::min(hw, hh);
+    // raise wsafe until the margin stays below 1/2 pixel wherever the test
+    // applies (w > wsafe, |X'|, |Y'| < win; the reciprocal may read 1 + rho
+    // high), which the error analysis assumes and the kernel relies on
+    const double room = 0.5 - kc * win - kd;
+    if (!(room > 0.0)) return;
+    ws = std::max(ws, 1.01 * (1 + rho) * (ka + kb * win) / room);
     if (!std::isfinite(ka) || !std::isfinite(ws) || ka > 1e30 || ws > 1e30) return;
     // round the constants up (the window down) so the float copies stay conservative
     p.fk[0] = (float)(ka * (1 + 1e-6));
@@ -189,7 +196,7 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     // inside |X'|, |Y'| < 8 min(W/2, H/2) every vertex lies far within the
     // guard band (|X - W/2| <= 128 W/2, likewise for Y), so the exact path
     // would not clip it
-    p.win = (float)(8.0 * std::min(hw, hh));
+    p.win = (float)win;
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

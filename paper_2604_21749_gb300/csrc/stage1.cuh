@@ -80,8 +80,9 @@ struct Tri9 { float v[9]; };    // the three vertices of a triangle
 // none either and the exact path would drop the triangle as well.
 // Evaluated without branches.
 __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
-    // vertex by vertex into running bounds (few live registers)
-    float xmn = INFINITY, xmx = -INFINITY, ymn = INFINITY, ymx = -INFINITY, wmn = INFINITY, rmx = 0.0f;
+    // vertex by vertex into running bounds (few live registers); the host
+    // chose wsafe so that every w > wsafe keeps the margin m below 1/2
+    float xmn, xmx, ymn, ymx, wmn, rmx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float x = p.v[3 * c], y = p.v[3 * c + 1], z = p.v[3 * c + 2];
@@ -91,14 +92,18 @@ __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
         const float w = __fmaf_rn(rw.x, x, __fmaf_rn(rw.y, y, __fmaf_rn(rw.z, z, rw.w)));
         const float r = rcp_approx(w);
         const float X = xw * r, Y = yw * r;
-        xmn = fminf(xmn, X); xmx = fmaxf(xmx, X);
-        ymn = fminf(ymn, Y); ymx = fmaxf(ymx, Y);
-        wmn = fminf(wmn, w); rmx = fmaxf(rmx, r);
+        if (c == 0) {
+            xmn = xmx = X; ymn = ymx = Y; wmn = w; rmx = r;
+        } else {
+            xmn = fminf(xmn, X); xmx = fmaxf(xmx, X);
+            ymn = fminf(ymn, Y); ymx = fmaxf(ymx, Y);
+            wmn = fminf(wmn, w); rmx = fmaxf(rmx, r);
+        }
     }
     const float4 k = fp.k, lim = fp.lim;
     const float a = fmaxf(fmaxf(fabsf(xmn), fabsf(xmx)), fmaxf(fabsf(ymn), fabsf(ymx)));
     const float m = __fmaf_rn(rmx, __fmaf_rn(k.y, a, k.x), __fmaf_rn(k.z, a, k.w));
-    const bool safe = (wmn > lim.x) & (a < lim.y) & (m < 0.5f);
+    const bool safe = (wmn > lim.x) & (a < lim.y);
     // no integer in [lo, hi] within [0, last] on one axis: floor(min(hi, last)) < max(lo, 0)
     const bool nx = floorf(fminf(xmx + m, lim.z)) < fmaxf(xmn - m, 0.0f);
     const bool ny = floorf(fminf(ymx + m, lim.w)) < fmaxf(ymn - m, 0.0f);
