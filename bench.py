@@ -354,7 +354,7 @@ def run_ours(args, ranks: Ranks):
         "e2e": {"value": round(total_tris / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gtris/s",
                 "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": args.W * args.H * 4},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": (3 + 2 * info["rounds"]) * args.steps,
         "clocks": clk,
         "frame_stats": {k: v for k, v in stats.items() if v},
     }
