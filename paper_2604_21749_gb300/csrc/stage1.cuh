@@ -359,12 +359,11 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
         const MeshDev mesh = S.mesh[slot];
         const uint32_t *idx = S.idx[slot];
         const uint32_t np = INST ? d.npairs : 1u;
-        if (!INST && !FUSED) {
-            // one pair per item; NT triangles per lane are loaded together (more
-            // loads in flight; the pair constants are read from shared memory,
-            // which leaves the registers to the loads)
+        if (!FUSED) {
+            // NT triangles per lane are loaded together (more loads in flight),
+            // then culled for every pair of the item; the pair constants are
+            // read from shared memory, which leaves the registers to the loads
             constexpr int NT = kNT;
-            const FastPair &fp = S.fp[slot][0];
             for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
                 bool valid[NT];
                 uint32_t ix[NT][3];
@@ -395,12 +394,15 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
                         for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
                     }
                 }
+                for (uint32_t pi = 0; pi < np; ++pi) {
+                    const FastPair &fp = S.fp[slot][pi];
 #pragma unroll
-                for (int u = 0; u < NT; ++u) {
-                    const bool live = valid[u] && !fast_cull(fp, p[u]);
-                    if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
-                    const unsigned m = __ballot_sync(0xffffffffu, live);
-                    if (k + u < tpt && lane == 0) f.bits[d.wbase + (k + u) * kConsumerWarps + warp] = m;
+                    for (int u = 0; u < NT; ++u) {
+                        const bool live = valid[u] && !fast_cull(fp, p[u]);
+                        if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
+                        const unsigned m = __ballot_sync(0xffffffffu, live);
+                        if (k + u < tpt && lane == 0) f.bits[d.wbase + pi * G + (k + u) * kConsumerWarps + warp] = m;
+                    }
                 }
             }
         } else
@@ -432,9 +434,7 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
                 const bool live = valid && !fast_cull(S.fp[slot][pi], p);
                 if (f.stats && valid && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
                 const unsigned m = __ballot_sync(0xffffffffu, live);
-                if (!FUSED) {
-                    if (lane == 0) f.bits[d.wbase + pi * G + k * kConsumerWarps + warp] = m;
-                } else if (m) {
+                if (m) {                               // fused: queue the survivors, run 32 at a time
                     if (f.stats && live) stat_add(f, kStatFast, 1);
                     if (live) wq[qn + __popc(m & lt_mask)] = make_uint2((uint32_t)(d.t0 + lt), d.pair0 + pi);
                     qn += __popc(m);
