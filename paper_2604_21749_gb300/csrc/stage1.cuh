@@ -110,6 +110,80 @@ __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
     return safe & (nx | ny);
 }
 
+// Packed FP32 pairs (Blackwell f32x2): two independent operations in one
+// instruction, each half rounded exactly like the scalar __fmaf_rn,
+// __fmul_rn, __fadd_rn and __fsub_rn.
+__device__ __forceinline__ float2 fma_x2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul_x2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 add_x2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub_x2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+
+// fast_cull for two triangles of the same pair at once: the same arithmetic,
+// with the FMA rows, the products by 1/w, the margin and the widened bounds
+// evaluated on packed pairs (one triangle per half).
+__device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, const Tri9 &q, bool &cp, bool &cq) {
+    float2 xmn, xmx, ymn, ymx, wmn, rmx;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 x = make_float2(p.v[3 * c], q.v[3 * c]);
+        const float2 y = make_float2(p.v[3 * c + 1], q.v[3 * c + 1]);
+        const float2 z = make_float2(p.v[3 * c + 2], q.v[3 * c + 2]);
+        const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw;
+        const float2 xw = fma_x2(dup(rx.x), x, fma_x2(dup(rx.y), y, fma_x2(dup(rx.z), z, dup(rx.w))));
+        const float2 yw = fma_x2(dup(ry.x), x, fma_x2(dup(ry.y), y, fma_x2(dup(ry.z), z, dup(ry.w))));
+        const float2 w = fma_x2(dup(rw.x), x, fma_x2(dup(rw.y), y, fma_x2(dup(rw.z), z, dup(rw.w))));
+        const float2 r = make_float2(rcp_approx(w.x), rcp_approx(w.y));
+        const float2 X = mul_x2(xw, r), Y = mul_x2(yw, r);
+        if (c == 0) {
+            xmn = xmx = X; ymn = ymx = Y; wmn = w; rmx = r;
+        } else {
+            xmn = make_float2(fminf(xmn.x, X.x), fminf(xmn.y, X.y));
+            xmx = make_float2(fmaxf(xmx.x, X.x), fmaxf(xmx.y, X.y));
+            ymn = make_float2(fminf(ymn.x, Y.x), fminf(ymn.y, Y.y));
+            ymx = make_float2(fmaxf(ymx.x, Y.x), fmaxf(ymx.y, Y.y));
+            wmn = make_float2(fminf(wmn.x, w.x), fminf(wmn.y, w.y));
+            rmx = make_float2(fmaxf(rmx.x, r.x), fmaxf(rmx.y, r.y));
+        }
+    }
+    const float4 k = fp.k, lim = fp.lim;
+    const float2 a = make_float2(fmaxf(fmaxf(fabsf(xmn.x), fabsf(xmx.x)), fmaxf(fabsf(ymn.x), fabsf(ymx.x))),
+                                 fmaxf(fmaxf(fabsf(xmn.y), fabsf(xmx.y)), fmaxf(fabsf(ymn.y), fabsf(ymx.y))));
+    const float2 m = fma_x2(rmx, fma_x2(dup(k.y), a, dup(k.x)), fma_x2(dup(k.z), a, dup(k.w)));
+    const float2 xh = add_x2(xmx, m), xl = sub_x2(xmn, m), yh = add_x2(ymx, m), yl = sub_x2(ymn, m);
+    const bool sp = (wmn.x > lim.x) & (a.x < lim.y), sq = (wmn.y > lim.x) & (a.y < lim.y);
+    const bool nxp = floorf(fminf(xh.x, lim.z)) < fmaxf(xl.x, 0.0f), nxq = floorf(fminf(xh.y, lim.z)) < fmaxf(xl.y, 0.0f);
+    const bool nyp = floorf(fminf(yh.x, lim.w)) < fmaxf(yl.x, 0.0f), nyq = floorf(fminf(yh.y, lim.w)) < fmaxf(yl.y, 0.0f);
+    cp = sp & (nxp | nyp);
+    cq = sq & (nxq | nyq);
+}
+
 // The exact path of one (triangle, pair) that the conservative cull kept:
 // indices and positions from global memory, FP32 transform in the fixed
 // order, clip outcodes, snap, culls, then stage-1 raster or queue 1.
@@ -395,10 +469,12 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
                     }
                 }
                 for (uint32_t pi = 0; pi < np; ++pi) {
-                    const FastPair &fp = S.fp[slot][pi];
+                    bool cull[NT];
+                    static_assert(NT == 2, "the cull evaluates triangles in packed pairs");
+                    fast_cull2(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
 #pragma unroll
                     for (int u = 0; u < NT; ++u) {
-                        const bool live = valid[u] && !fast_cull(fp, p[u]);
+                        const bool live = valid[u] && !cull[u];
                         if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
                         const unsigned m = __ballot_sync(0xffffffffu, live);
                         if (k + u < tpt && lane == 0) f.bits[d.wbase + pi * G + (k + u) * kConsumerWarps + warp] = m;
