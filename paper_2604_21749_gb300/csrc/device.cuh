@@ -275,8 +275,15 @@ __device__ __forceinline__ uint64_t frag_key(int64_t E0, int64_t E1, int64_t E2,
     return ((uint64_t)(__float_as_uint(depth) >> 3) << 36) | (id & kIdMask);
 }
 
-// Section 3.1: the closest fragment wins by a 64-bit atomic minimum.  A
-// plain read first skips the atomic when the stored word is already
+// Section 3.1: the closest fragment wins by a 64-bit atomic minimum.
+// Stage 1's tiny triangles cover a pixel or two each: a reduction that needs
+// no answer, issued directly.
+__device__ __forceinline__ void depth_min(uint64_t *vis, size_t pix, uint64_t key) {
+    atomicMin(reinterpret_cast<unsigned long long *>(vis + pix), (unsigned long long)key);
+}
+
+// Stages 2 and 3 write many pixels of one triangle, often behind nearer
+// ones: a plain read first skips the atomic when the stored word is already
 // smaller (words only ever decrease, so a stale read is still safe).
 __device__ __forceinline__ void depth_test_write(uint64_t *vis, size_t pix, uint64_t key) {
     unsigned long long *p = reinterpret_cast<unsigned long long *>(vis + pix);

@@ -124,7 +124,7 @@ __device__ __forceinline__ void raster_small(const int X[3], const int Y[3], con
                                     __fmul_rn(__int2float_rn(r2), iz[2]));
                 float depth = __fdiv_rn(fA, s);
                 uint64_t key = ((uint64_t)(__float_as_uint(depth) >> 3) << 36) | (id & kIdMask);
-                depth_test_write(row, (size_t)x, key);
+                depth_min(row, (size_t)x, key);
             }
             r0 -= dy0 * 256; r1 -= dy1 * 256; r2 -= dy2 * 256;
         }
