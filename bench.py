@@ -423,10 +423,20 @@ def batched_vs_plain(args, dev):
     tp = timeit(plain)
     same = all(torch.equal(v[4], p) for v, p in zip(views, plain_out))
     r.sync()
+    # one more batched frame outside the graph for per-stage times, one with counters
+    r.render_batch(views, use_graph=False)
+    st = r.stage_times()
+    r.set_config(collect_stats=1)
+    r.render_batch(views, use_graph=False)
+    stats = r.sync()
+    r.set_config(collect_stats=0)
     out = {"workload": name, "batched_ms": round(tb, 3), "plain_ms": round(tp, 3),
            "speedup": round(tp / tb, 3), "identical": bool(same), "pairs": info["pairs"],
-           "triangle_instance_views": info["triangles"],
-           "batched_gtris_s": round(info["triangles"] / (tb * 1e-3) / 1e9, 2), "generation_s": round(tgen, 1)}
+           "rounds": info["rounds"], "triangle_instance_views": info["triangles"],
+           "batched_gtris_s": round(info["triangles"] / (tb * 1e-3) / 1e9, 2),
+           "batched_stage_ms": {k: round(v, 3) for k, v in
+                                zip(["clear", "stage1_cull", "stage1_exact", "stage2", "stage3"], st)},
+           "batched_stats": {k: v for k, v in stats.items() if v}, "generation_s": round(tgen, 1)}
     r.close()
     del sc, views, plain_out
     torch.cuda.empty_cache()

@@ -211,7 +211,7 @@ curast_config default_config() {
     c.pairs_per_segment = 64;
     c.queue1_capacity = 1ull << 22;
     c.queue2_capacity = 1ull << 21;
-    c.stage1_bitmap_bytes = 1ull << 30;
+    c.stage1_bitmap_bytes = 1ull << 32;
     c.check_indices = 1;
     c.collect_stats = 0;
     return c;
