@@ -45,6 +45,8 @@ def parse_args():
     p.add_argument("--batched", choices=["full", "small", "off"], default="full",
                    help="also time the batched multi-mesh path against one launch per mesh per view")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-supersampling", dest="supersampling", action="store_false",
+                   help="skip the 2x2 / 4x4 super-sampled frames")
     p.add_argument("--subset", type=int, default=0,
                    help="profiling aid: give geometry only to this many tiles next to the view centre "
                         "(same layout, camera and triangle density; the other tiles are empty)")
@@ -358,6 +360,8 @@ def run_ours(args, ranks: Ranks):
         "clocks": clk,
         "frame_stats": {k: v for k, v in stats.items() if v},
     }
+    if ranks.rank == 0 and ranks.world == 1 and args.supersampling:
+        result["supersampling"] = supersampling(r, cam, args, ms_frame, stream)
     r.close()
     del sc, vis
     torch.cuda.empty_cache()
@@ -370,6 +374,34 @@ def run_ours(args, ranks: Ranks):
                                   "sample": f"three adjacent central tiles ({n} triangles) of the same frame, "
                                             f"single-threaded oracle, {dt:.1f} s"}
     return result
+
+
+def supersampling(r, cam, args, ms_1x1, stream):
+    """Anti-aliasing by super sampling (the paper's Table 5 on this frame):
+    the same view rendered at 2x2 and 4x4 samples per pixel, then the
+    box-filtered resolve to the output size; frame ms of each (render only)
+    and of the resolve."""
+    import torch
+    out = {"1x1_ms": round(ms_1x1, 3)}
+    for ss in (2, 4):
+        W, H = ss * args.W, ss * args.H
+        vis = r.new_vis(W, H)
+        r.render(cam.view, cam.proj, W, H, vis)
+        r.sync()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        frames = 3
+        e0.record(stream)
+        for _ in range(frames):
+            r.render(cam.view, cam.proj, W, H, vis)
+        e1.record(stream)
+        r.resolve_ss(cam.view, cam.proj, vis, ss, want_f32=False)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        out[f"{ss}x{ss}_ms"] = round(e0.elapsed_time(e1) / frames, 3)
+        out[f"{ss}x{ss}_resolve_ms"] = round(e1.elapsed_time(e2), 3)
+        del vis
+        torch.cuda.empty_cache()
+    return out
 
 
 def batched_vs_plain(args, dev):

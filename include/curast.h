@@ -196,6 +196,17 @@ curast_status curast_render_batch(curast_ctx *ctx, const curast_view *views, int
 curast_status curast_resolve(curast_ctx *ctx, const float view[16], const float proj[16], int W, int H,
                              const uint64_t *vis, float *rgba_f32, uint8_t *rgba8, curast_stream stream);
 
+/* Super-sampled resolve (anti-aliasing by super sampling, Section 5): vis
+ * holds the view rendered by curast_render at (ss W) x (ss H), i.e. an
+ * ss x ss grid of samples at the sub-pixel centres of every output pixel.
+ * Each sample is resolved as by curast_resolve; output pixel (x, y) is the
+ * box filter of its samples -- FP32 colours summed row by row (sample rows
+ * outer, columns inner) and divided by ss^2 -- then converted to RGBA8 as
+ * by curast_resolve.  W, H: the output size; ss: 1..8 with ss W, ss H <=
+ * 16384; ss = 1 is curast_resolve.  Buffers as for curast_resolve. */
+curast_status curast_resolve_ss(curast_ctx *ctx, const float view[16], const float proj[16], int W, int H, int ss,
+                                const uint64_t *vis, float *rgba_f32, uint8_t *rgba8, curast_stream stream);
+
 /* --------------------------------------------------- differentiable step --- */
 
 /* Forward of the differentiable interpolation (perspective-correct

@@ -539,6 +539,39 @@ int orc_resolve(const orc_mesh *meshes, int n_meshes, const orc_instance *inst, 
     return ORC_OK;
 }
 
+/* Anti-aliasing by super sampling (Section 5): the view is rendered and
+ * resolved at ss times the output size per axis (fine, FP32 RGBA,
+ * (ss W) x (ss H) pixels); output pixel (x, y) is the box filter of its
+ * ss x ss samples -- summed one IEEE float addition at a time, sample rows
+ * outer and columns inner, then divided by ss^2 -- and RGBA8 =
+ * rint(clamp(c, 0, 1) * 255) as for the plain resolve. */
+int orc_box_filter(const float *fine, int W, int H, int ss, float *rgba, uint8_t *rgba8)
+{
+    if (ss < 1 || W < 1 || H < 1) return ORC_BAD_ARG;
+    const int Wf = ss * W;
+    const float n = (float)(ss * ss);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t pix = (size_t)y * (size_t)W + (size_t)x;
+            for (int ch = 0; ch < 4; ++ch) {
+                float sum = 0.0f;
+                for (int sy = 0; sy < ss; ++sy)
+                    for (int sx = 0; sx < ss; ++sx) {
+                        size_t f = (size_t)(ss * y + sy) * (size_t)Wf + (size_t)(ss * x + sx);
+                        sum = sum + fine[4 * f + ch];
+                    }
+                float c = sum / n;
+                if (rgba) rgba[4 * pix + ch] = c;
+                if (rgba8) {
+                    if (!(c >= 0.0f)) c = 0.0f;
+                    if (c > 1.0f) c = 1.0f;
+                    rgba8[4 * pix + ch] = (uint8_t)rintf(c * 255.0f);
+                }
+            }
+        }
+    return ORC_OK;
+}
+
 /* Interpolation of a C-channel float attribute of one mesh (the
  * differentiable forward): pixels whose triangle belongs to an instance of
  * mesh `mesh` get sum_k b_k attr_k; all others get zero.  The barycentrics

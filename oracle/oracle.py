@@ -68,6 +68,7 @@ def _lib():
             L.orc_interpolate.argtypes = [C.POINTER(_Mesh), C.c_int, C.POINTER(_Instance), C.c_int,
                                           C.POINTER(_Camera), C.c_void_p, C.c_uint32, C.c_void_p, C.c_int,
                                           C.c_void_p, C.c_void_p]
+            L.orc_box_filter.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_camera_params.argtypes = [C.c_void_p, C.c_void_p]
             L.orc_model_view.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_clip.argtypes = [C.c_void_p, C.c_float, C.c_void_p]
@@ -164,6 +165,26 @@ def resolve(osc: OracleScene, camera, vis: np.ndarray):
     if st != 0:
         raise ValueError(f"orc_resolve failed: {st}")
     return rgba, rgba8
+
+
+def box_filter(fine: np.ndarray, ss: int):
+    """Box filter of an (ss H, ss W, 4) FP32 image to (H, W, 4) FP32 and RGBA8."""
+    fine = np.ascontiguousarray(fine, np.float32)
+    Hs, Ws = fine.shape[:2]
+    H, W = Hs // ss, Ws // ss
+    rgba = np.zeros((H, W, 4), np.float32)
+    rgba8 = np.zeros((H, W, 4), np.uint8)
+    st = _lib().orc_box_filter(fine.ctypes.data, W, H, ss, rgba.ctypes.data, rgba8.ctypes.data)
+    if st != 0:
+        raise ValueError(f"orc_box_filter failed: {st}")
+    return rgba, rgba8
+
+
+def resolve_ss(osc: OracleScene, camera_fine, vis_fine: np.ndarray, ss: int):
+    """Super-sampled resolve: the resolve of the (ss W) x (ss H) render,
+    box-filtered to W x H."""
+    fine, _ = resolve(osc, camera_fine, vis_fine)
+    return box_filter(fine, ss)
 
 
 def interpolate(osc: OracleScene, camera, vis: np.ndarray, mesh: int, attr):

@@ -26,7 +26,7 @@ STATUS_NAMES = {
 STATIC_MAX_INSTANCES = 32
 EXPORTS = ["curast_create", "curast_destroy", "curast_status_string", "curast_get_config", "curast_set_config",
            "curast_upload_mesh", "curast_update_mesh", "curast_add_instance", "curast_clear_instances",
-           "curast_clear", "curast_render", "curast_render_mesh", "curast_render_batch", "curast_resolve",
+           "curast_clear", "curast_render", "curast_render_mesh", "curast_render_batch", "curast_resolve", "curast_resolve_ss",
            "curast_interpolate", "curast_interpolate_backward", "curast_sync", "curast_stage_times",
            "curast_autotune", "curast_last_frame", "curast_render_static"]
 
@@ -105,6 +105,7 @@ def load(build: bool = False, path: Optional[str] = None) -> C.CDLL:
             "curast_render_mesh": [vp, u32, fp, fp, i32, i32, vp, vp],
             "curast_render_batch": [vp, C.POINTER(View), i32, i32, vp],
             "curast_resolve": [vp, fp, fp, i32, i32, vp, vp, vp, vp],
+            "curast_resolve_ss": [vp, fp, fp, i32, i32, i32, vp, vp, vp, vp],
             "curast_interpolate": [vp, u32, vp, fp, fp, i32, i32, vp, vp, i32, vp, vp],
             "curast_interpolate_backward": [vp, u32, vp, fp, fp, i32, i32, vp, vp, i32, vp, vp, vp, vp],
             "curast_sync": [vp, vp, C.POINTER(Stats)],
@@ -280,6 +281,20 @@ class Renderer:
         u8 = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device) if want_rgba8 else None
         _check(self.L.curast_resolve(self._h, _mat(view), _mat(proj), W, H, _ptr(vis), _ptr(f32), _ptr(u8),
                                      _stream(stream)), "curast_resolve")
+        return f32, u8
+
+    def resolve_ss(self, view, proj, vis: torch.Tensor, ss: int, want_f32: bool = True, want_rgba8: bool = True,
+                   stream=None):
+        """Box-filtered resolve of a view rendered at ss times the output
+        size per axis; returns the (H, W) output images."""
+        Hs, Ws = vis.shape
+        if Hs % ss or Ws % ss:
+            raise ValueError("the super-sampled buffer must be ss times the output size")
+        H, W = Hs // ss, Ws // ss
+        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device) if want_f32 else None
+        u8 = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device) if want_rgba8 else None
+        _check(self.L.curast_resolve_ss(self._h, _mat(view), _mat(proj), W, H, ss, _ptr(vis), _ptr(f32), _ptr(u8),
+                                        _stream(stream)), "curast_resolve_ss")
         return f32, u8
 
     # ------------------------------------------------------- differentiable

@@ -40,6 +40,7 @@ struct ShadeArgs {
     // resolve
     float *rgba_f32;
     uint8_t *rgba8;
+    int ss;                     // super-sampled resolve: samples per pixel axis
     // interpolate
     uint32_t mesh;
     const float *pos;           // overrides the mesh's positions when non-null
@@ -52,6 +53,8 @@ struct ShadeArgs {
 };
 
 cudaError_t launch_resolve(const ShadeArgs &a, cudaStream_t s);
+// a.W, a.H: the super-sampled buffer (ss W x ss H); W, H: the output
+cudaError_t launch_resolve_ss(const ShadeArgs &a, int W, int H, cudaStream_t s);
 cudaError_t launch_interpolate(const ShadeArgs &a, cudaStream_t s);
 cudaError_t launch_interpolate_backward(const ShadeArgs &a, cudaStream_t s);
 

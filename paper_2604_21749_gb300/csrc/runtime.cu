@@ -854,6 +854,23 @@ curast_status curast_resolve(curast_ctx *c, const float view[16], const float pr
     return CURAST_OK;
 }
 
+curast_status curast_resolve_ss(curast_ctx *c, const float view[16], const float proj[16], int W, int H, int ss,
+                                const uint64_t *vis, float *rgba_f32, uint8_t *rgba8, curast_stream stream) {
+    if (!c || ss < 1 || ss > 8 || W < 1 || H < 1 || W > 16384 / ss || H > 16384 / ss) return CURAST_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(rgba_f32) & 15) || (reinterpret_cast<uintptr_t>(rgba8) & 3))
+        return CURAST_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ShadeArgs a;
+    curast_status st = shade_setup(c, view, proj, ss * W, ss * H, vis, &a, s);
+    if (st != CURAST_OK) return st;
+    a.rgba_f32 = rgba_f32;
+    a.rgba8 = rgba8;
+    a.ss = ss;
+    CU(launch_resolve_ss(a, W, H, s));
+    return CURAST_OK;
+}
+
 curast_status curast_interpolate(curast_ctx *c, uint32_t mesh_id, const float *pos, const float view[16],
                                  const float proj[16], int W, int H, const uint64_t *vis, const float *attr, int C,
                                  float *out, curast_stream stream) {

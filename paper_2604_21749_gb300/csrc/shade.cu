@@ -93,16 +93,16 @@ __device__ __forceinline__ bool lookup(const ShadeArgs &a, uint64_t key, PixelTr
 }
 
 // ---------------------------------------------------------------- resolve --
-__global__ void __launch_bounds__(256) k_resolve(ShadeArgs a) {
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (x >= a.W || y >= a.H) return;
-    const size_t pix = (size_t)y * a.W + x;
-    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+// Colour of the sample at pixel (x, y) of a W x H visibility buffer:
+// barycentrics of the pixel-centre ray, vertex colours byte / 255; 0 where
+// the pixel is empty or the mesh has no colours.
+__device__ __forceinline__ void resolve_sample(const ShadeArgs &a, int x, int y, int W, int H, float c[4]) {
+    c[0] = c[1] = c[2] = c[3] = 0.0f;
     PixelTri pt;
     MeshDev m;
-    if (lookup(a, a.vis[pix], pt, m) && m.rgba) {
+    if (lookup(a, a.vis[(size_t)y * W + x], pt, m) && m.rgba) {
         float b0, b1, b2;
-        ray_bary(pixel_ray(x, y, a.W, a.H, a.fx, a.fy), pt.v[0], pt.v[1], pt.v[2], b0, b1, b2);
+        ray_bary(pixel_ray(x, y, W, H, a.fx, a.fy), pt.v[0], pt.v[1], pt.v[2], b0, b1, b2);
         const uchar4 q0 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[0]];
         const uchar4 q1 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[1]];
         const uchar4 q2 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[2]];
@@ -113,6 +113,9 @@ __global__ void __launch_bounds__(256) k_resolve(ShadeArgs a) {
             c[ch] = interp3(b0, b1, b2, __fdiv_rn(__uint2float_rn(s0[ch]), 255.0f),
                             __fdiv_rn(__uint2float_rn(s1[ch]), 255.0f), __fdiv_rn(__uint2float_rn(s2[ch]), 255.0f));
     }
+}
+
+__device__ __forceinline__ void store_rgba(const ShadeArgs &a, size_t pix, const float c[4]) {
     if (a.rgba_f32) reinterpret_cast<float4 *>(a.rgba_f32)[pix] = make_float4(c[0], c[1], c[2], c[3]);
     if (a.rgba8) {
         unsigned char q[4];
@@ -121,6 +124,36 @@ __global__ void __launch_bounds__(256) k_resolve(ShadeArgs a) {
             q[ch] = (unsigned char)__float2uint_rn(__fmul_rn(fminf(fmaxf(c[ch], 0.0f), 1.0f), 255.0f));
         reinterpret_cast<uchar4 *>(a.rgba8)[pix] = make_uchar4(q[0], q[1], q[2], q[3]);
     }
+}
+
+__global__ void __launch_bounds__(256) k_resolve(ShadeArgs a) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= a.W || y >= a.H) return;
+    float c[4];
+    resolve_sample(a, x, y, a.W, a.H, c);
+    store_rgba(a, (size_t)y * a.W + x, c);
+}
+
+// Super-sampled resolve: the visibility buffer holds (ss W) x (ss H)
+// samples (the same view rendered at ss times the resolution per axis);
+// output pixel (x, y) is the box filter of its ss x ss samples -- their
+// colours summed row by row, y outer and x inner, then divided by ss^2.
+__global__ void __launch_bounds__(256) k_resolve_ss(ShadeArgs a, int W, int H) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= W || y >= H) return;
+    const int ss = a.ss;
+    float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int sy = 0; sy < ss; ++sy)
+        for (int sx = 0; sx < ss; ++sx) {
+            float c[4];
+            resolve_sample(a, ss * x + sx, ss * y + sy, a.W, a.H, c);
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) sum[ch] = __fadd_rn(sum[ch], c[ch]);
+        }
+    const float n = __int2float_rn(ss * ss);
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) sum[ch] = __fdiv_rn(sum[ch], n);
+    store_rgba(a, (size_t)y * W + x, sum);
 }
 
 // ------------------------------------------------------- interpolate fwd --
@@ -246,6 +279,11 @@ __global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
 
 // -------------------------------------------------------------- launchers --
 static dim3 pixel_grid(int W, int H) { return dim3((unsigned)((W + 31) / 32), (unsigned)((H + 7) / 8)); }
+
+cudaError_t launch_resolve_ss(const ShadeArgs &a, int W, int H, cudaStream_t s) {
+    k_resolve_ss<<<pixel_grid(W, H), 256, 0, s>>>(a, W, H);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_resolve(const ShadeArgs &a, cudaStream_t s) {
     k_resolve<<<pixel_grid(a.W, a.H), 256, 0, s>>>(a);

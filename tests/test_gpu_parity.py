@@ -78,6 +78,29 @@ def test_stage_choices_never_change_visibility(api, small, cfg):
     del keep
 
 
+@pytest.mark.parametrize("ss", [1, 2, 4])
+def test_supersampled_resolve_equals_oracle(api, small, ss):
+    """Super sampling: the view rendered at ss times the resolution per axis
+    (bit-exact), box-filtered by curast_resolve_ss (within 1e-6, RGBA8 equal)."""
+    cam = small.cameras[0]
+    fine = Camera(cam.view, cam.proj, ss * cam.W, ss * cam.H)
+    r = _renderer(api)
+    keep = upload(r, small)
+    vis = r.render(fine.view, fine.proj, fine.W, fine.H)
+    f32, u8 = r.resolve_ss(cam.view, cam.proj, vis, ss)
+    r.sync()
+    osc = orc.OracleScene(small)
+    ref = orc.render(osc, fine)
+    assert_vis_equal(vis, ref, f"ss={ss}")
+    rf, r8 = orc.resolve_ss(osc, fine, ref, ss)
+    np.testing.assert_allclose(f32.cpu().numpy(), rf, atol=1e-6, rtol=0)
+    np.testing.assert_array_equal(u8.cpu().numpy(), r8)
+    if ss == 1:
+        g32, g8 = r.resolve(cam.view, cam.proj, vis)
+        assert torch.equal(g32, f32) and torch.equal(g8, u8)
+    del keep
+
+
 def _mixed_scene():
     meshes = [S.heightfield_mesh(40, seed=11), S.sphere_mesh(12, seed=12), S.heightfield_mesh(7, seed=13),
               Mesh(pos=torch.zeros((3, 3)), idx=torch.zeros((0, 3), dtype=torch.int32),

@@ -49,6 +49,8 @@ C_MUTATIONS = [
     ("resolve, pixel centre", "float ndx = ((float)(2 * x + 1) / (float)cam->W) - 1.0f;",
      "float ndx = ((float)(2 * x) / (float)cam->W) - 1.0f;"),
     ("interpolation, wrong colour index", "    float q = b[1] * c1;", "    float q = b[1] * c2;"),
+    ("box filter, divides by ss", "    const float n = (float)(ss * ss);", "    const float n = (float)(ss);"),
+    ("box filter, wrong sample row", "size_t f = (size_t)(ss * y + sy) * (size_t)Wf", "size_t f = (size_t)(ss * y + sx) * (size_t)Wf"),
 ]
 
 PY_MUTATIONS = [

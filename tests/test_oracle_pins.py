@@ -502,6 +502,39 @@ def test_id_space_overflow_is_rejected(oracle_lib):
     assert int(ok[-1]) == (1 << 36) - 1
 
 
+# ---------------------------------------------------------- super sampling ---
+def test_box_filter_identity_mean_and_half_coverage(oracle_lib):
+    """ss = 1 is the plain resolve; the box filter is the mean of the ss x ss
+    samples (float64 reference); a triangle edge between sample columns
+    covers exactly half of every pixel's samples."""
+    O = oracle_lib
+    rng = np.random.default_rng(21)
+    fine = rng.uniform(0, 1, size=(6, 10, 4)).astype(np.float32)
+    r1, q1 = O.box_filter(fine, 1)
+    np.testing.assert_array_equal(r1, fine)
+    np.testing.assert_array_equal(q1, np.rint(fine * 255).astype(np.uint8))
+    r2, _ = O.box_filter(fine, 2)
+    ref = fine.astype(np.float64).reshape(3, 2, 5, 2, 4).mean(axis=(1, 3))
+    np.testing.assert_allclose(r2, ref, rtol=0, atol=3e-7)
+    # a camera-facing quad whose right edge runs between the two sample
+    # columns of every pixel (ss = 2): colour / 2 in every covered pixel
+    W, H, ss, D = 8, 6, 2, 2.0
+    t = math.tan(math.radians(30.0))
+    hx, hy = D * t * W / H, D * t                 # half extents of the view at depth D
+    xr = -hx + 2 * hx * (2 * 3 + 1) / (ss * W)    # boundary between sample columns 6 and 7
+    pos = [[-2 * hx, -2 * hy, -D], [xr, -2 * hy, -D], [-2 * hx, 2 * hy, -D], [xr, 2 * hy, -D]]
+    col = np.full((4, 4), 200, np.uint8)
+    sc = Scene([mesh_np(pos, [[0, 1, 2], [1, 3, 2]], col)], [Instance(0, ident())])
+    cam = _cam(np.eye(4), S.perspective(60, W / H, 0.01, 100.0), ss * W, ss * H)
+    osc = O.OracleScene(sc)
+    vis = O.render(osc, cam)
+    r, _ = O.resolve_ss(osc, cam, vis, ss)
+    c = 200.0 / 255.0      # constant colour: barycentric interpolation is exact to a few ulps
+    np.testing.assert_allclose(r[:, :3, :], c, rtol=0, atol=4e-7)
+    np.testing.assert_allclose(r[:, 3, :], c / 2, rtol=0, atol=4e-7)
+    np.testing.assert_array_equal(r[:, 4:, :], 0)
+
+
 # --------------------------------------------------------------- adjoint ---
 def _small_diff_scene():
     sc, col = S.scene_differentiable(n=20, W=72, H=64)
