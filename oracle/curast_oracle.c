@@ -539,6 +539,69 @@ int orc_resolve(const orc_mesh *meshes, int n_meshes, const orc_instance *inst, 
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------ compression */
+
+/* Section 4.6, indices: the number of bits for indices in [min, max] is
+ * ceil(log2(span + 1)), span = max - min (span + 1 distinct values; the
+ * paper's ceil(log2(span)) undercounts when span is a power of two). */
+int orc_index_bits(uint32_t span)
+{
+    int b = 0;
+    while (b < 32 && ((uint64_t)1 << b) < (uint64_t)span + 1) ++b;
+    return b;
+}
+
+/* Packs n indices as (index - min) in `bits` bits each, index k at bit
+ * k * bits of a little-endian stream of 32-bit words (words must hold
+ * ceil(n * bits / 32) + 1 zeroed words). */
+void orc_pack_indices(const uint32_t *idx, uint64_t n, uint32_t imin, int bits, uint32_t *words)
+{
+    for (uint64_t k = 0; k < n; ++k) {
+        uint64_t v = (uint64_t)(idx[k] - imin);
+        for (int b = 0; b < bits; ++b) {
+            uint64_t bit = k * (uint64_t)bits + (uint64_t)b;
+            if ((v >> b) & 1u) words[bit >> 5] |= 1u << (bit & 31);
+        }
+    }
+}
+
+/* Index k of a packed stream: min + the `bits` bits at bit k * bits. */
+void orc_unpack_indices(const uint32_t *words, uint64_t n, uint32_t imin, int bits, uint32_t *idx)
+{
+    for (uint64_t k = 0; k < n; ++k) {
+        uint64_t v = 0;
+        for (int b = 0; b < bits; ++b) {
+            uint64_t bit = k * (uint64_t)bits + (uint64_t)b;
+            v |= (uint64_t)((words[bit >> 5] >> (bit & 31)) & 1u) << b;
+        }
+        idx[k] = imin + (uint32_t)v;
+    }
+}
+
+/* Section 4.6, positions: 16-bit fixed point over the mesh bounds.  Per
+ * axis, with lo the minimum and size = max - min (in double),
+ * q = rint(65535 (p - lo) / size) clamped to [0, 65535] (q = 0 when
+ * size = 0), in double; the paper's 65536 would overflow 16 bits at
+ * p = max.  The decoded position is fma(q, step, lo) in FP32 with
+ * step = (float)(size / 65535); it is what every stage renders. */
+void orc_quantize_positions(const float *pos, uint64_t V, const float lo[3], const double size[3], uint16_t *q)
+{
+    for (uint64_t i = 0; i < V; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double v = 0.0;
+            if (size[a] > 0.0) v = rint(65535.0 * (((double)pos[3 * i + a] - (double)lo[a]) / size[a]));
+            if (!(v >= 0.0)) v = 0.0;
+            if (v > 65535.0) v = 65535.0;
+            q[3 * i + a] = (uint16_t)v;
+        }
+}
+
+void orc_dequantize_positions(const uint16_t *q, uint64_t V, const float lo[3], const float step[3], float *pos)
+{
+    for (uint64_t i = 0; i < V; ++i)
+        for (int a = 0; a < 3; ++a) pos[3 * i + a] = fmaf((float)q[3 * i + a], step[a], lo[a]);
+}
+
 /* Anti-aliasing by super sampling (Section 5): the view is rendered and
  * resolved at ss times the output size per axis (fine, FP32 RGBA,
  * (ss W) x (ss H) pixels); output pixel (x, y) is the box filter of its

@@ -69,6 +69,12 @@ def _lib():
                                           C.POINTER(_Camera), C.c_void_p, C.c_uint32, C.c_void_p, C.c_int,
                                           C.c_void_p, C.c_void_p]
             L.orc_box_filter.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+            L.orc_index_bits.argtypes = [C.c_uint32]
+            L.orc_index_bits.restype = C.c_int
+            L.orc_pack_indices.argtypes = [C.c_void_p, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
+            L.orc_unpack_indices.argtypes = [C.c_void_p, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
+            L.orc_quantize_positions.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_dequantize_positions.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_camera_params.argtypes = [C.c_void_p, C.c_void_p]
             L.orc_model_view.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_clip.argtypes = [C.c_void_p, C.c_float, C.c_void_p]
@@ -165,6 +171,63 @@ def resolve(osc: OracleScene, camera, vis: np.ndarray):
     if st != 0:
         raise ValueError(f"orc_resolve failed: {st}")
     return rgba, rgba8
+
+
+# ------------------------------------------------------------ compression --
+def index_bits(span: int) -> int:
+    return int(_lib().orc_index_bits(span))
+
+
+def pack_indices(idx, imin: int, bits: int) -> np.ndarray:
+    idx = np.ascontiguousarray(idx, np.uint32).reshape(-1)
+    words = np.zeros((idx.size * bits + 31) // 32 + 1, np.uint32)
+    _lib().orc_pack_indices(idx.ctypes.data, idx.size, imin, bits, words.ctypes.data)
+    return words
+
+
+def unpack_indices(words, n: int, imin: int, bits: int) -> np.ndarray:
+    words = np.ascontiguousarray(words, np.uint32)
+    out = np.zeros(n, np.uint32)
+    _lib().orc_unpack_indices(words.ctypes.data, n, imin, bits, out.ctypes.data)
+    return out
+
+
+def quantize_positions(pos, lo, size):
+    pos = np.ascontiguousarray(pos, np.float32).reshape(-1, 3)
+    lo = np.ascontiguousarray(lo, np.float32)
+    size = np.ascontiguousarray(size, np.float64)
+    q = np.zeros(pos.shape, np.uint16)
+    _lib().orc_quantize_positions(pos.ctypes.data, pos.shape[0], lo.ctypes.data, size.ctypes.data, q.ctypes.data)
+    return q
+
+
+def dequantize_positions(q, lo, step):
+    q = np.ascontiguousarray(q, np.uint16).reshape(-1, 3)
+    lo = np.ascontiguousarray(lo, np.float32)
+    step = np.ascontiguousarray(step, np.float32)
+    out = np.zeros(q.shape, np.float32)
+    _lib().orc_dequantize_positions(q.ctypes.data, q.shape[0], lo.ctypes.data, step.ctypes.data, out.ctypes.data)
+    return out
+
+
+def compress_mesh(pos, idx):
+    """The Section 4.6 encoding of a mesh and the mesh it decodes to:
+    returns (fields, decoded positions, decoded indices).  Bounds are the
+    per-axis min / max of the positions; size and step as described at
+    orc_quantize_positions."""
+    pos = np.ascontiguousarray(pos, np.float32).reshape(-1, 3)
+    idx = np.ascontiguousarray(idx, np.uint32).reshape(-1)
+    lo = pos.min(axis=0).astype(np.float32)
+    hi = pos.max(axis=0).astype(np.float32)
+    size = hi.astype(np.float64) - lo.astype(np.float64)
+    step = (size / 65535.0).astype(np.float32)
+    imin = int(idx.min()) if idx.size else 0
+    imax = int(idx.max()) if idx.size else 0
+    bits = index_bits(imax - imin)
+    q = quantize_positions(pos, lo, size)
+    words = pack_indices(idx, imin, bits)
+    fields = {"lo": lo, "step": step, "size": size, "imin": imin, "bits": bits, "q": q, "words": words}
+    return fields, dequantize_positions(q, lo, step), unpack_indices(words, idx.size, imin, bits)
 
 
 def box_filter(fine: np.ndarray, ss: int):

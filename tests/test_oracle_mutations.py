@@ -51,6 +51,12 @@ C_MUTATIONS = [
     ("interpolation, wrong colour index", "    float q = b[1] * c1;", "    float q = b[1] * c2;"),
     ("box filter, divides by ss", "    const float n = (float)(ss * ss);", "    const float n = (float)(ss);"),
     ("box filter, wrong sample row", "size_t f = (size_t)(ss * y + sy) * (size_t)Wf", "size_t f = (size_t)(ss * y + sx) * (size_t)Wf"),
+    ("index bits, log2 of the span", "((uint64_t)1 << b) < (uint64_t)span + 1", "((uint64_t)1 << b) < (uint64_t)span"),
+    ("index packing, shifted stream", "uint64_t bit = k * (uint64_t)bits + (uint64_t)b;\n            if ((v >> b) & 1u)",
+     "uint64_t bit = k * (uint64_t)bits + (uint64_t)b + 1;\n            if ((v >> b) & 1u)"),
+    ("quantization, 65536 levels", "v = rint(65535.0 * (", "v = rint(65536.0 * ("),
+    ("dequantization, lo dropped", "pos[3 * i + a] = fmaf((float)q[3 * i + a], step[a], lo[a]);",
+     "pos[3 * i + a] = fmaf((float)q[3 * i + a], step[a], 0.0f);"),
 ]
 
 PY_MUTATIONS = [

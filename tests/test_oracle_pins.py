@@ -502,6 +502,82 @@ def test_id_space_overflow_is_rejected(oracle_lib):
     assert int(ok[-1]) == (1 << 36) - 1
 
 
+# ------------------------------------------------------------- compression ---
+def test_compression_golden_examples(oracle_lib):
+    """The paper's worked examples (tests/golden/compression.txt): indices
+    2500..3000 take 9 bits; 16 bits over 65 m resolve 1 mm."""
+    O = oracle_lib
+    rows = _golden_rows("compression.txt")
+    kinds = {r[0] for r in rows}
+    assert kinds == {"index", "position"}
+    for r in rows:
+        if r[0] == "index":
+            assert O.index_bits(int(r[2]) - int(r[1])) == int(r[3])
+        else:
+            span, prec = float(r[1]), float(r[2])
+            pos = np.array([[0, 0, 0], [span, 1, 1]], np.float32)
+            f, dec, _ = O.compress_mesh(pos, np.array([0, 1, 1], np.uint32))
+            assert float(f["step"][0]) <= prec
+            np.testing.assert_allclose(dec, pos, rtol=0, atol=prec / 2 + 1e-5)
+
+
+def test_index_packing_round_trip_and_bit_layout(oracle_lib):
+    """Packing is exact for every width 0..32, and the stream holds index k's
+    bits at k * bits, little-endian (checked against a bit-matrix layout);
+    a span that is a power of two needs one bit more than log2(span)."""
+    O = oracle_lib
+    rng = np.random.default_rng(31)
+    assert O.index_bits(512) == 10 and O.index_bits(511) == 9 and O.index_bits(0) == 0
+    for bits in list(range(0, 33)):
+        span = (1 << bits) - 1
+        imin = int(rng.integers(0, 2**32 - span)) if bits < 32 else 0
+        n = 97
+        idx = (imin + rng.integers(0, span + 1, size=n, dtype=np.uint64)).astype(np.uint32)
+        if bits > 0:
+            idx[0], idx[1] = imin, imin + span
+        assert O.index_bits(int(idx.max()) - int(idx.min())) == (bits if bits > 0 else 0)
+        words = O.pack_indices(idx, imin, bits)
+        np.testing.assert_array_equal(O.unpack_indices(words, n, imin, bits), idx)
+        # independent layout: a bits-wide little-endian bit matrix, flattened
+        v = (idx.astype(np.uint64) - imin)
+        m = ((v[:, None] >> np.arange(bits, dtype=np.uint64)[None, :]) & 1).astype(np.uint8).reshape(-1)
+        m = np.concatenate([m, np.zeros((-m.size) % 32 + 32, np.uint8)])
+        ref = np.packbits(m.reshape(-1, 32)[:, ::-1], axis=1).view(">u4").reshape(-1)
+        np.testing.assert_array_equal(words[:ref.size], ref)
+
+
+def test_position_quantization_error_and_ends(oracle_lib):
+    """Decoded positions lie within half a step (plus FP32 rounding) of the
+    originals; the minimum decodes exactly; a flat axis decodes to its value."""
+    O = oracle_lib
+    rng = np.random.default_rng(32)
+    pos = np.stack([rng.uniform(-3.0, 5.0, 5000), rng.uniform(10.0, 10.5, 5000), np.full(5000, 2.25)], 1)
+    pos = pos.astype(np.float32)
+    f, dec, _ = O.compress_mesh(pos, np.arange(3, dtype=np.uint32))
+    step = f["step"].astype(np.float64)
+    err = np.abs(dec.astype(np.float64) - pos.astype(np.float64))
+    tol = step / 2 + 4 * np.finfo(np.float32).eps * np.abs(pos).max(axis=0)
+    assert (err <= tol).all()
+    i = np.argmin(pos[:, 0])
+    assert dec[i, 0] == pos[i, 0]
+    assert (dec[:, 2] == np.float32(2.25)).all()
+
+
+def test_positions_on_the_grid_survive_compression(oracle_lib):
+    """Positions that are decoded grid points (fma(q, step, lo)) quantize back
+    to the same q, so encoding them loses nothing."""
+    O = oracle_lib
+    rng = np.random.default_rng(33)
+    lo = np.array([-2.5, 0.0, 7.0], np.float32)
+    size = np.array([8.0, 0.75, 3.0], np.float64)
+    step = (size / 65535.0).astype(np.float32)
+    q = rng.integers(0, 65536, size=(4000, 3)).astype(np.uint16)
+    q[0] = 0
+    q[1] = 65535
+    pos = O.dequantize_positions(q, lo, step)
+    np.testing.assert_array_equal(O.quantize_positions(pos, lo, size), q)
+
+
 # ---------------------------------------------------------- super sampling ---
 def test_box_filter_identity_mean_and_half_coverage(oracle_lib):
     """ss = 1 is the plain resolve; the box filter is the mean of the ss x ss
