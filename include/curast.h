@@ -134,9 +134,22 @@ curast_status curast_set_config(curast_ctx *ctx, const curast_config *cfg);
  *   pos    device, V x 3 FP32 (x, y, z), 4-byte aligned
  *   idx    device, T x 3 uint32 vertex indices, triangles wound CCW = front
  *   rgba8  device, V x 4 bytes of vertex colour for curast_resolve, or NULL
- *   flags  must be 0
+ *   flags  0, or CURAST_MESH_COMPRESSED
  * The buffers are BORROWED: they must stay allocated until curast_destroy;
- * their contents may change between renders.  T may be 0. */
+ * their contents may change between renders.  T may be 0.
+ *
+ * CURAST_MESH_COMPRESSED (Section 4.6) encodes the mesh on the device into
+ * buffers the context owns, and pos and idx are read only during this call
+ * (rgba8 stays borrowed):
+ *   indices  bit-packed as (index - min) in ceil(log2(max - min + 1)) bits
+ *            each, index k at bit k * bits of little-endian 32-bit words;
+ *   positions  16 bits an axis over the mesh bounds lo..hi, per axis
+ *            q = rint(65535 (p - lo) / (hi - lo)) computed in double.
+ * Every stage then renders the decoded positions fma(q, step, lo) in FP32,
+ * step = (float)((hi - lo) / 65535), and the decoded indices.  Meshes whose
+ * indices reach V are rejected with CURAST_ERR_INDEX_OUT_OF_RANGE.  A
+ * compressed mesh cannot be updated and has no differentiable path. */
+#define CURAST_MESH_COMPRESSED 1u
 curast_status curast_upload_mesh(curast_ctx *ctx, const float *pos, uint64_t V, const uint32_t *idx,
                                  uint64_t T, const uint8_t *rgba8, uint32_t flags, uint32_t *mesh_id);
 
@@ -144,6 +157,23 @@ curast_status curast_upload_mesh(curast_ctx *ctx, const float *pos, uint64_t V, 
  * positions for the differentiable path).  NULL keeps the current one. */
 curast_status curast_update_mesh(curast_ctx *ctx, uint32_t mesh_id, const float *pos, const uint32_t *idx,
                                  const uint8_t *rgba8);
+
+/* How a registered mesh is held.  For a compressed mesh the encoding's
+ * parameters and read-only device pointers to the context's buffers. */
+typedef struct {
+    uint64_t V, T;
+    uint32_t compressed;          /* 1: Section 4.6 encoding held by the context              */
+    uint32_t index_bits;          /* bits per index (compressed)                              */
+    uint32_t index_min;
+    uint32_t pad;
+    float pos_lo[3];              /* decoded position = fma(q, pos_step, pos_lo) per axis     */
+    float pos_step[3];
+    uint64_t geometry_bytes;      /* device bytes of the index and position data a frame reads */
+    const void *packed_indices;   /* device: ceil(3 T bits / 32) words, then zero padding     */
+    const void *quantized_positions; /* device: V x 3 uint16                                  */
+} curast_mesh_info;
+
+curast_status curast_get_mesh_info(const curast_ctx *ctx, uint32_t mesh_id, curast_mesh_info *out);
 
 /* Adds an instance of a mesh with an affine model matrix (Section 4.5).
  * Its ids start at the running total of triangles of the instances added

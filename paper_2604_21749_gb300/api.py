@@ -26,7 +26,7 @@ STATUS_NAMES = {
 STATIC_MAX_INSTANCES = 32
 EXPORTS = ["curast_create", "curast_destroy", "curast_status_string", "curast_get_config", "curast_set_config",
            "curast_upload_mesh", "curast_update_mesh", "curast_add_instance", "curast_clear_instances",
-           "curast_clear", "curast_render", "curast_render_mesh", "curast_render_batch", "curast_resolve", "curast_resolve_ss",
+           "curast_clear", "curast_render", "curast_render_mesh", "curast_render_batch", "curast_resolve", "curast_resolve_ss", "curast_get_mesh_info",
            "curast_interpolate", "curast_interpolate_backward", "curast_sync", "curast_stage_times",
            "curast_autotune", "curast_last_frame", "curast_render_static"]
 
@@ -64,6 +64,21 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class MeshInfo(C.Structure):
+    _fields_ = [("V", C.c_uint64), ("T", C.c_uint64), ("compressed", C.c_uint32), ("index_bits", C.c_uint32),
+                ("index_min", C.c_uint32), ("pad", C.c_uint32), ("pos_lo", C.c_float * 3), ("pos_step", C.c_float * 3),
+                ("geometry_bytes", C.c_uint64), ("packed_indices", C.c_void_p), ("quantized_positions", C.c_void_p)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        d["pos_lo"] = list(self.pos_lo)
+        d["pos_step"] = list(self.pos_step)
+        return d
+
+
+MESH_COMPRESSED = 1
+
+
 class FrameInfo(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("segments", C.c_uint64), ("work_items", C.c_uint64),
                 ("triangles", C.c_uint64), ("unique_triangles", C.c_uint64), ("unique_vertices", C.c_uint64),
@@ -97,6 +112,7 @@ def load(build: bool = False, path: Optional[str] = None) -> C.CDLL:
             "curast_get_config": [vp, C.POINTER(Config)],
             "curast_set_config": [vp, C.POINTER(Config)],
             "curast_upload_mesh": [vp, vp, u64, vp, u64, vp, u32, C.POINTER(u32)],
+            "curast_get_mesh_info": [vp, u32, C.POINTER(MeshInfo)],
             "curast_update_mesh": [vp, u32, vp, vp, vp],
             "curast_add_instance": [vp, u32, fp, C.POINTER(u32)],
             "curast_clear_instances": [vp],
@@ -196,7 +212,10 @@ class Renderer:
         return c
 
     # ---------------------------------------------------------------- scene
-    def upload_mesh(self, pos: torch.Tensor, idx: torch.Tensor, rgba8: Optional[torch.Tensor] = None) -> int:
+    def upload_mesh(self, pos: torch.Tensor, idx: torch.Tensor, rgba8: Optional[torch.Tensor] = None,
+                    compressed: bool = False) -> int:
+        """Registers a mesh; compressed=True keeps only the Section 4.6
+        encoding (the context owns it; pos and idx may be freed after)."""
         _need(pos, torch.float32, "pos", self.device)
         if idx.dtype not in (torch.int32, torch.uint32):
             raise ValueError("idx must hold uint32 (int32 tensor)")
@@ -204,9 +223,10 @@ class Renderer:
         if rgba8 is not None:
             _need(rgba8, torch.uint8, "rgba8", self.device)
         mid = C.c_uint32()
-        _check(self.L.curast_upload_mesh(self._h, _ptr(pos), pos.shape[0], _ptr(idx), idx.shape[0], _ptr(rgba8), 0,
+        flags = MESH_COMPRESSED if compressed else 0
+        _check(self.L.curast_upload_mesh(self._h, _ptr(pos), pos.shape[0], _ptr(idx), idx.shape[0], _ptr(rgba8), flags,
                                          C.byref(mid)), "curast_upload_mesh")
-        self._keep[("mesh", mid.value)] = (pos, idx, rgba8)
+        self._keep[("mesh", mid.value)] = (None, None, rgba8) if compressed else (pos, idx, rgba8)
         self._mesh_T.append(int(idx.shape[0]))
         return mid.value
 
@@ -327,6 +347,11 @@ class Renderer:
         st = Stats()
         _check(self.L.curast_sync(self._h, _stream(stream), C.byref(st)), "curast_sync")
         return st.as_dict()
+
+    def mesh_info(self, mesh: int) -> dict:
+        mi = MeshInfo()
+        _check(self.L.curast_get_mesh_info(self._h, mesh, C.byref(mi)), "curast_get_mesh_info")
+        return mi.as_dict()
 
     def last_frame(self) -> dict:
         fi = FrameInfo()

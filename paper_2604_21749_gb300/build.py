@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["raster.cu", "shade.cu", "runtime.cu", "static_render.cu"]
+SOURCES = ["raster.cu", "shade.cu", "runtime.cu", "static_render.cu", "compress.cu"]
 HEADERS = ["device.cuh", "internal.h", "stage1.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -61,11 +61,41 @@ struct RoundDev {
 constexpr int kMaxRounds = 64;
 
 struct MeshDev {
-    const float *pos;
-    const uint32_t *idx;
+    const float *pos;        // V x 3 FP32, or nullptr when compressed
+    const uint32_t *idx;     // T x 3 uint32, or nullptr when compressed
     const uint8_t *rgba;
     uint64_t V, T;
+    // Section 4.6 compression (cidx != nullptr): index k of the 3T index
+    // words is imin + the `bits` bits at bit k * bits of cidx (little-endian
+    // 32-bit words); vertex i is fma(qpos[3i + a], step[a], lo[a]) in FP32
+    const uint32_t *cidx;
+    const uint16_t *qpos;
+    uint32_t bits, mask, imin, pad;
+    float lo[3], step[3];
 };
+
+__device__ __forceinline__ bool compressed(const MeshDev &m) { return m.cidx != nullptr; }
+
+// Index word k (= 3 t + corner) of a mesh, decoded when compressed.
+__device__ __forceinline__ uint32_t mesh_index(const MeshDev &m, uint64_t k) {
+    if (!m.cidx) return __ldg(m.idx + k);
+    const uint64_t bit = k * m.bits;
+    const uint32_t *w = m.cidx + (bit >> 5);
+    return m.imin + (__funnelshift_r(__ldg(w), __ldg(w + 1), (uint32_t)bit & 31u) & m.mask);
+}
+
+// The three coordinates of vertex i as every stage renders them.
+__device__ __forceinline__ void mesh_vertex(const MeshDev &m, uint32_t i, float &x, float &y, float &z) {
+    if (!m.qpos) {
+        const float *q = m.pos + 3 * (uint64_t)i;
+        x = __ldg(q); y = __ldg(q + 1); z = __ldg(q + 2);
+    } else {
+        const uint16_t *q = m.qpos + 3 * (uint64_t)i;
+        x = __fmaf_rn(__uint2float_rn(__ldg(q)), m.step[0], m.lo[0]);
+        y = __fmaf_rn(__uint2float_rn(__ldg(q + 1)), m.step[1], m.lo[1]);
+        z = __fmaf_rn(__uint2float_rn(__ldg(q + 2)), m.step[2], m.lo[2]);
+    }
+}
 
 struct Q1Entry {             // stage 1 -> stage 2: a whole triangle of one pair
     uint64_t id;

@@ -7,7 +7,7 @@
 namespace curast {
 
 struct LaunchShape {
-    int stage1_blocks_per_sm[2][2];   // [instanced][fused]
+    int stage1_blocks_per_sm[2][3];   // [instanced][variant: 0 cull, 1 fused, 2 cull of compressed meshes]
     int stage1x_blocks_per_sm;        // exact kernel of stage 1
     int stage2_blocks_per_sm;
     int stage3_blocks_per_sm;
@@ -19,12 +19,18 @@ cudaError_t query_launch_shape(LaunchShape *out, int device);
 cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s);
 // Stage 1 of round r: the cull kernel (fused: it runs the exact path itself
 // and needs no bitmap), then the exact kernel over the round's bitmap.
-cudaError_t launch_stage1(const FrameDev &f, bool instanced, bool fused, uint32_t r, int blocks, cudaStream_t s);
+cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32_t r, int blocks, cudaStream_t s);
 cudaError_t launch_stage1_exact(const FrameDev &f, uint32_t r, int blocks, cudaStream_t s);
 cudaError_t launch_stage2(const FrameDev &f, int blocks, cudaStream_t s);
 cudaError_t launch_stage3(const FrameDev &f, int blocks, cudaStream_t s);
 // scratch: 256 * 6 floats; out6: xmin ymin zmin xmax ymax zmax
 cudaError_t launch_aabb(const float *pos, uint64_t V, float *scratch, float *out6, cudaStream_t s);
+// Section 4.6 encoding (compress.cu)
+cudaError_t launch_minmax_u32(const uint32_t *v, uint64_t n, unsigned *out2, cudaStream_t s);
+cudaError_t launch_pack_indices(const uint32_t *idx, uint64_t n, uint32_t imin, uint32_t bits, uint32_t *words,
+                                uint64_t nwords, cudaStream_t s);
+cudaError_t launch_quantize_positions(const float *pos, uint64_t V, const double lo[3], const double size[3],
+                                      uint16_t *q, cudaStream_t s);
 cudaError_t launch_count_diff(const uint64_t *a, const uint64_t *b, uint64_t n, unsigned long long *out,
                               cudaStream_t s);
 

@@ -51,8 +51,9 @@ __device__ __forceinline__ void load_clip(const FrameDev &f, const MeshDev &mesh
                                           const ViewDev &vw, CV c[3]) {
     const float *mv = f.pairs[pidx].mv;
     for (int k = 0; k < 3; ++k) {
-        const float *q = mesh.pos + 3 * (uint64_t)mesh.idx[3 * t + k];
-        c[k] = to_clip(mv, q[0], q[1], q[2], vw.fx, vw.fy);
+        float x, y, z;
+        mesh_vertex(mesh, mesh_index(mesh, 3 * t + k), x, y, z);
+        c[k] = to_clip(mv, x, y, z, vw.fx, vw.fy);
     }
 }
 
@@ -345,21 +346,23 @@ __global__ void k_aabb_final(const float *part, int n, float *out) {
 }
 
 // -------------------------------------------------------------- launchers --
-template <bool INST, bool FUSED>
+template <bool INST, bool FUSED, bool COMP>
 cudaError_t stage1_shape(int *blocks) {
     const size_t sm = stage1_smem_bytes<INST, FUSED>();
-    cudaError_t e = cudaFuncSetAttribute(k_stage1<INST, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_stage1<INST, FUSED, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_stage1<INST, FUSED>, s1::kThreads, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_stage1<INST, FUSED, COMP>, s1::kThreads, sm);
 }
 
 cudaError_t query_launch_shape(LaunchShape *o, int device) {
     cudaError_t e = cudaDeviceGetAttribute(&o->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    if ((e = stage1_shape<false, false>(&o->stage1_blocks_per_sm[0][0])) != cudaSuccess) return e;
-    if ((e = stage1_shape<false, true>(&o->stage1_blocks_per_sm[0][1])) != cudaSuccess) return e;
-    if ((e = stage1_shape<true, false>(&o->stage1_blocks_per_sm[1][0])) != cudaSuccess) return e;
-    if ((e = stage1_shape<true, true>(&o->stage1_blocks_per_sm[1][1])) != cudaSuccess) return e;
+    if ((e = stage1_shape<false, false, false>(&o->stage1_blocks_per_sm[0][0])) != cudaSuccess) return e;
+    if ((e = stage1_shape<false, true, false>(&o->stage1_blocks_per_sm[0][1])) != cudaSuccess) return e;
+    if ((e = stage1_shape<false, false, true>(&o->stage1_blocks_per_sm[0][2])) != cudaSuccess) return e;
+    if ((e = stage1_shape<true, false, false>(&o->stage1_blocks_per_sm[1][0])) != cudaSuccess) return e;
+    if ((e = stage1_shape<true, true, false>(&o->stage1_blocks_per_sm[1][1])) != cudaSuccess) return e;
+    if ((e = stage1_shape<true, false, true>(&o->stage1_blocks_per_sm[1][2])) != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1x_blocks_per_sm, k_stage1_exact, 32 * s1::kExactWarps, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage2_blocks_per_sm, k_stage2, 256, 0);
@@ -377,11 +380,18 @@ cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_stage1(const FrameDev &f, bool instanced, bool fused, uint32_t r, int blocks, cudaStream_t s) {
-    if (instanced && fused) k_stage1<true, true><<<blocks, s1::kThreads, stage1_smem_bytes<true, true>(), s>>>(f, r);
-    else if (instanced) k_stage1<true, false><<<blocks, s1::kThreads, stage1_smem_bytes<true, false>(), s>>>(f, r);
-    else if (fused) k_stage1<false, true><<<blocks, s1::kThreads, stage1_smem_bytes<false, true>(), s>>>(f, r);
-    else k_stage1<false, false><<<blocks, s1::kThreads, stage1_smem_bytes<false, false>(), s>>>(f, r);
+cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32_t r, int blocks, cudaStream_t s) {
+    const size_t s0 = stage1_smem_bytes<false, false>(), s1f = stage1_smem_bytes<false, true>();
+    const size_t i0 = stage1_smem_bytes<true, false>(), i1f = stage1_smem_bytes<true, true>();
+    if (instanced) {
+        if (variant == 1) k_stage1<true, true, false><<<blocks, s1::kThreads, i1f, s>>>(f, r);
+        else if (variant == 2) k_stage1<true, false, true><<<blocks, s1::kThreads, i0, s>>>(f, r);
+        else k_stage1<true, false, false><<<blocks, s1::kThreads, i0, s>>>(f, r);
+    } else {
+        if (variant == 1) k_stage1<false, true, false><<<blocks, s1::kThreads, s1f, s>>>(f, r);
+        else if (variant == 2) k_stage1<false, false, true><<<blocks, s1::kThreads, s0, s>>>(f, r);
+        else k_stage1<false, false, false><<<blocks, s1::kThreads, s0, s>>>(f, r);
+    }
     return cudaGetLastError();
 }
 

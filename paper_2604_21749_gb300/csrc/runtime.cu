@@ -66,6 +66,13 @@ struct MeshRec {
     uint64_t V, T;
     bool bounded;
     double lo[3], hi[3];
+    // Section 4.6 encoding, owned by the context (comp)
+    bool comp = false;
+    uint32_t *cidx = nullptr;
+    uint16_t *qpos = nullptr;
+    uint64_t cwords = 0;
+    uint32_t bits = 0, imin = 0;
+    float clo[3] = {0, 0, 0}, cstep[3] = {0, 0, 0};
 };
 
 struct InstRec {
@@ -252,6 +259,7 @@ struct curast_ctx {
     DevBuf<Q1Entry> d_q1;
     DevBuf<uint32_t> d_bits;              // survivor bitmap of one stage-1 round
     std::vector<RoundDev> rounds;
+    std::vector<char> round_comp;         // the round's meshes are compressed
     DevBuf<Q2Entry> d_q2;
     Counters *d_ctr = nullptr;
     unsigned *d_err = nullptr;
@@ -304,11 +312,24 @@ curast_status sync_scene(curast_ctx *c, cudaStream_t s) {
     if (c->meshes_dirty) {
         std::vector<MeshDev> md(c->meshes.size());
         for (size_t i = 0; i < md.size(); ++i) {
-            md[i].pos = c->meshes[i].pos;
-            md[i].idx = c->meshes[i].idx;
-            md[i].rgba = c->meshes[i].rgba;
-            md[i].V = c->meshes[i].V;
-            md[i].T = c->meshes[i].T;
+            const MeshRec &r = c->meshes[i];
+            md[i] = MeshDev{};
+            md[i].pos = r.pos;
+            md[i].idx = r.idx;
+            md[i].rgba = r.rgba;
+            md[i].V = r.V;
+            md[i].T = r.T;
+            if (r.comp) {
+                md[i].cidx = r.cidx;
+                md[i].qpos = r.qpos;
+                md[i].bits = r.bits;
+                md[i].mask = r.bits >= 32 ? ~0u : (1u << r.bits) - 1u;
+                md[i].imin = r.imin;
+                for (int a = 0; a < 3; ++a) {
+                    md[i].lo[a] = r.clo[a];
+                    md[i].step[a] = r.cstep[a];
+                }
+            }
         }
         const bool grow = md.size() > c->d_meshes.cap;
         CU(c->d_meshes.reserve(std::max<size_t>(md.size(), 1)));
@@ -390,8 +411,14 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
             c->hs.push_back(s);
         }
     }
-    // heavy work items (many pairs) first so the tail of the persistent loop is light
-    std::stable_sort(c->hs.begin(), c->hs.end(), [](const SegDev &a, const SegDev &b) { return a.npairs > b.npairs; });
+    // uncompressed meshes first, then compressed ones (rounds hold one kind, so
+    // each runs the cull kernel built for it); within each, heavy work items
+    // (many pairs) first so the tail of the persistent loop is light
+    std::stable_sort(c->hs.begin(), c->hs.end(), [c](const SegDev &a, const SegDev &b) {
+        const bool ca = c->meshes[a.mesh].comp, cb = c->meshes[b.mesh].comp;
+        if (ca != cb) return cb;
+        return a.npairs > b.npairs;
+    });
     // survivor-bitmap words: per item, npairs x (per_item / 32)
     const uint64_t G = per_item / 32;
     uint64_t nb = 0, nw = 0;
@@ -405,18 +432,29 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
         c->instanced = c->instanced || s.npairs > 1;
     }
     // rounds: runs of items whose bitmap fits the configured size (grown
-    // when the frame would need more than kMaxRounds rounds)
+    // when the frame would need more than kMaxRounds rounds; one round more
+    // may start where the meshes turn from uncompressed to compressed)
     uint64_t cap = std::max<uint64_t>(c->cfg.stage1_bitmap_bytes / 4, 64 * G);
-    cap = std::max<uint64_t>(cap, (nw + kMaxRounds - 1) / kMaxRounds + 64 * G);
+    cap = std::max<uint64_t>(cap, (nw + kMaxRounds - 3) / (kMaxRounds - 2) + 64 * G);
     c->rounds.clear();
+    c->round_comp.clear();
     RoundDev cur{0, 0, 0, 0};
+    bool cur_comp = false;
     for (const SegDev &s : c->hs) {
         const uint64_t items = (s.T + per_item - 1) / per_item, wpi = s.npairs * G;
+        const bool comp = c->meshes[s.mesh].comp;
+        if (comp != cur_comp && cur.b1 > cur.b0) {           // a round holds one kind of mesh
+            c->rounds.push_back(cur);
+            c->round_comp.push_back(cur_comp);
+            cur = RoundDev{cur.b1, cur.b1, cur.w1, cur.w1};
+        }
+        cur_comp = comp;
         uint64_t done = 0;
         while (done < items) {
             uint64_t room = (cap - (cur.w1 - cur.w0)) / wpi;
             if (room == 0) {
                 c->rounds.push_back(cur);
+                c->round_comp.push_back(cur_comp);
                 cur = RoundDev{cur.b1, cur.b1, cur.w1, cur.w1};
                 room = cap / wpi;
             }
@@ -426,7 +464,10 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
             done += take;
         }
     }
-    if (cur.b1 > cur.b0 || c->rounds.empty()) c->rounds.push_back(cur);
+    if (cur.b1 > cur.b0 || c->rounds.empty()) {
+        c->rounds.push_back(cur);
+        c->round_comp.push_back(cur_comp);
+    }
     if (c->rounds.size() > (size_t)kMaxRounds) return CURAST_ERR_INVALID_ARG;   // unreachable by the cap above
     uint64_t maxw = 1;
     for (const RoundDev &r : c->rounds) maxw = std::max(maxw, r.w1 - r.w0);
@@ -516,7 +557,9 @@ curast_status enqueue_stages(curast_ctx *c, bool clear, bool timing, cudaStream_
     // kernel empties it (ev[2] falls after the last round's cull)
     const uint32_t nr = (uint32_t)c->rounds.size();
     for (uint32_t r = 0; r < nr; ++r) {
-        CU(launch_stage1(f, c->instanced, false, r, sms * c->shape.stage1_blocks_per_sm[c->instanced ? 1 : 0][0], s));
+        const int variant = c->round_comp[r] ? 2 : 0;
+        CU(launch_stage1(f, c->instanced, variant, r, sms * c->shape.stage1_blocks_per_sm[c->instanced ? 1 : 0][variant],
+                         s));
         if (timing && r + 1 == nr) CU(cudaEventRecord(c->ev[2], s));
         CU(launch_stage1_exact(f, r, sms * c->shape.stage1x_blocks_per_sm, s));
     }
@@ -542,6 +585,7 @@ curast_status render_views(curast_ctx *c, const curast_view *views, int nv, long
     std::vector<uint64_t> key = {(uint64_t)nv, (uint64_t)c->instanced, (uint64_t)clear,
                                  (uint64_t)(uintptr_t)c->d_tab.p, (uint64_t)(uintptr_t)c->d_meshes.p,
                                  (uint64_t)(uintptr_t)c->d_bits.p, (uint64_t)c->rounds.size()};
+    for (char rc : c->round_comp) key.push_back((uint64_t)rc);
     for (int v = 0; v < nv; ++v) {
         key.push_back((uint64_t)views[v].W);
         key.push_back((uint64_t)views[v].H);
@@ -632,6 +676,75 @@ curast_status compute_bounds(curast_ctx *c, MeshRec &m) {
     return CURAST_OK;
 }
 
+int index_bits(uint32_t span) {
+    int b = 0;
+    while (b < 32 && (1ull << b) < (uint64_t)span + 1) ++b;
+    return b;
+}
+
+void free_compressed(MeshRec &m) {
+    if (m.cidx) cudaFree(m.cidx);
+    if (m.qpos) cudaFree(m.qpos);
+    m.cidx = nullptr;
+    m.qpos = nullptr;
+}
+
+// Section 4.6 encoding of an uploaded mesh into context-owned buffers (see
+// CURAST_MESH_COMPRESSED); m.lo / m.hi hold the bounds of the positions.
+curast_status compress_mesh(curast_ctx *c, MeshRec &m) {
+    uint32_t imin = 0, imax = 0;
+    if (m.T > 0) {
+        unsigned init[2] = {~0u, 0u}, mm[2];
+        CU(cudaMemcpyAsync(c->d_aabb, init, sizeof(init), cudaMemcpyHostToDevice, c->aux));
+        CU(launch_minmax_u32(m.idx, 3 * m.T, reinterpret_cast<unsigned *>(c->d_aabb), c->aux));
+        CU(cudaMemcpyAsync(mm, c->d_aabb, sizeof(mm), cudaMemcpyDeviceToHost, c->aux));
+        CU(cudaStreamSynchronize(c->aux));
+        imin = mm[0];
+        imax = mm[1];
+        if (imax >= m.V) return CURAST_ERR_INDEX_OUT_OF_RANGE;
+    }
+    m.bits = (uint32_t)index_bits(imax - imin);
+    m.imin = imin;
+    // words of the stream, then padding: the cull reads one word ahead and
+    // rounds its copies up to 16 bytes
+    m.cwords = ((3 * m.T * m.bits + 31) >> 5) + 8;
+    double lo[3], size[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = m.bounded ? (double)(float)m.lo[a] : 0.0;
+        size[a] = m.bounded ? (double)(float)m.hi[a] - lo[a] : 0.0;
+        m.clo[a] = (float)lo[a];
+        m.cstep[a] = (float)(size[a] / 65535.0);
+    }
+    uint32_t *w = nullptr;
+    uint16_t *q = nullptr;
+    CU(cudaMalloc(reinterpret_cast<void **>(&w), m.cwords * sizeof(uint32_t)));
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&q), std::max<uint64_t>(3 * m.V, 8) * sizeof(uint16_t));
+    if (e != cudaSuccess) {
+        cudaFree(w);
+        return e == cudaErrorMemoryAllocation ? CURAST_ERR_OUT_OF_MEMORY : CURAST_ERR_CUDA;
+    }
+    m.cidx = w;
+    m.qpos = q;
+    cudaError_t e1 = cudaMemsetAsync(w, 0, m.cwords * sizeof(uint32_t), c->aux);
+    if (e1 == cudaSuccess && m.T) e1 = launch_pack_indices(m.idx, 3 * m.T, imin, m.bits, w, m.cwords - 8, c->aux);
+    if (e1 == cudaSuccess && m.V) e1 = launch_quantize_positions(m.pos, m.V, lo, size, q, c->aux);
+    if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(c->aux);
+    if (e1 != cudaSuccess) {
+        free_compressed(m);
+        return CURAST_ERR_CUDA;
+    }
+    m.comp = true;
+    m.pos = nullptr;      // the caller's buffers are no longer read
+    m.idx = nullptr;
+    // bounds of the decoded positions fma(q, step, lo), q <= 65535, for culling
+    for (int a = 0; a < 3; ++a) {
+        m.lo[a] = (double)m.clo[a] - 1e-6 * std::fabs((double)m.clo[a]);
+        m.hi[a] = (double)m.clo[a] + 65535.0 * (double)m.cstep[a];
+        m.hi[a] += 1e-6 * std::fabs(m.hi[a]);
+    }
+    return CURAST_OK;
+}
+
 bool valid_config(const curast_config &c) {
     return c.stage1_max_pixels >= 1 && c.stage1_max_pixels <= 1024 && c.stage2_max_pixels >= 32 &&
            c.tile_log2 >= 4 && c.tile_log2 <= 7 && c.stage1_tri_per_thread >= 1 && c.stage1_tri_per_thread <= 4 &&
@@ -702,6 +815,7 @@ void curast_destroy(curast_ctx *c) {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     invalidate_graph(c);
+    for (MeshRec &m : c->meshes) free_compressed(m);
     c->d_meshes.release();
     c->d_base.release();
     c->d_inst_mesh.release();
@@ -744,7 +858,7 @@ curast_status curast_set_config(curast_ctx *c, const curast_config *cfg) {
 
 curast_status curast_upload_mesh(curast_ctx *c, const float *pos, uint64_t V, const uint32_t *idx, uint64_t T,
                                  const uint8_t *rgba8, uint32_t flags, uint32_t *mesh_id) {
-    if (!c || !mesh_id || flags != 0) return CURAST_ERR_INVALID_ARG;
+    if (!c || !mesh_id || (flags & ~CURAST_MESH_COMPRESSED)) return CURAST_ERR_INVALID_ARG;
     if ((V > 0 && !pos) || (T > 0 && !idx) || V > 0xFFFFFFFFull || T > 0xFFFFFFFFull) return CURAST_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(pos) & 3) || (reinterpret_cast<uintptr_t>(idx) & 3) ||
         (reinterpret_cast<uintptr_t>(rgba8) & 3))
@@ -758,6 +872,10 @@ curast_status curast_upload_mesh(curast_ctx *c, const float *pos, uint64_t V, co
     m.T = T;
     curast_status st = compute_bounds(c, m);
     if (st != CURAST_OK) return st;
+    if (flags & CURAST_MESH_COMPRESSED) {
+        st = compress_mesh(c, m);
+        if (st != CURAST_OK) return st;
+    }
     c->meshes.push_back(m);
     c->meshes_dirty = true;
     c->inst_dirty = true;
@@ -770,12 +888,36 @@ curast_status curast_update_mesh(curast_ctx *c, uint32_t mesh_id, const float *p
     if (!c || mesh_id >= c->meshes.size()) return CURAST_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     MeshRec &m = c->meshes[mesh_id];
+    if (m.comp && (pos || idx)) return CURAST_ERR_INVALID_ARG;
     if (pos) m.pos = pos;
     if (idx) m.idx = idx;
     if (rgba8) m.rgba = rgba8;
     curast_status st = compute_bounds(c, m);
     if (st != CURAST_OK) return st;
     c->meshes_dirty = true;
+    return CURAST_OK;
+}
+
+curast_status curast_get_mesh_info(const curast_ctx *c, uint32_t mesh_id, curast_mesh_info *out) {
+    if (!c || !out || mesh_id >= c->meshes.size()) return CURAST_ERR_INVALID_ARG;
+    const MeshRec &m = c->meshes[mesh_id];
+    std::memset(out, 0, sizeof(*out));
+    out->V = m.V;
+    out->T = m.T;
+    out->compressed = m.comp ? 1u : 0u;
+    if (m.comp) {
+        out->index_bits = m.bits;
+        out->index_min = m.imin;
+        for (int a = 0; a < 3; ++a) {
+            out->pos_lo[a] = m.clo[a];
+            out->pos_step[a] = m.cstep[a];
+        }
+        out->geometry_bytes = ((3 * m.T * m.bits + 31) >> 5) * 4 + 6 * m.V;
+        out->packed_indices = m.cidx;
+        out->quantized_positions = m.qpos;
+    } else {
+        out->geometry_bytes = 12 * m.T + 12 * m.V;
+    }
     return CURAST_OK;
 }
 
@@ -875,6 +1017,7 @@ curast_status curast_interpolate(curast_ctx *c, uint32_t mesh_id, const float *p
                                  const float proj[16], int W, int H, const uint64_t *vis, const float *attr, int C,
                                  float *out, curast_stream stream) {
     if (!c || mesh_id >= c->meshes.size() || !attr || !out || C < 1 || C > 16) return CURAST_ERR_INVALID_ARG;
+    if (c->meshes[mesh_id].comp) return CURAST_ERR_INVALID_ARG;     // no differentiable path
     DeviceGuard g(c->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ShadeArgs a;
@@ -894,6 +1037,7 @@ curast_status curast_interpolate_backward(curast_ctx *c, uint32_t mesh_id, const
                                           int C, const float *grad_out, float *grad_attr, float *grad_pos,
                                           curast_stream stream) {
     if (!c || mesh_id >= c->meshes.size() || !attr || !grad_out || C < 1 || C > 16) return CURAST_ERR_INVALID_ARG;
+    if (c->meshes[mesh_id].comp) return CURAST_ERR_INVALID_ARG;     // no differentiable path
     DeviceGuard g(c->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ShadeArgs a;

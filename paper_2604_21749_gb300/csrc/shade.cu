@@ -83,12 +83,20 @@ __device__ __forceinline__ bool lookup(const ShadeArgs &a, uint64_t key, PixelTr
     m = a.meshes[a.inst_mesh[i]];
     if (o.t >= m.T) return false;
     const float *mv = a.inst_mv + 12 * (size_t)i;
-    const float *pos = (a.pos && a.inst_mesh[i] == a.mesh) ? a.pos : m.pos;
+    const bool over = a.pos && a.inst_mesh[i] == a.mesh;    // positions given by the caller
     for (int k = 0; k < 3; ++k) {
-        o.vi[k] = m.idx[3 * o.t + k];
+        o.vi[k] = mesh_index(m, 3 * o.t + k);
         if (o.vi[k] >= m.V) return false;
     }
-    for (int k = 0; k < 3; ++k) o.v[k] = view_space(mv, pos + 3 * (size_t)o.vi[k]);
+    for (int k = 0; k < 3; ++k) {
+        float p[3];
+        if (over) {
+            p[0] = a.pos[3 * (size_t)o.vi[k]]; p[1] = a.pos[3 * (size_t)o.vi[k] + 1]; p[2] = a.pos[3 * (size_t)o.vi[k] + 2];
+        } else {
+            mesh_vertex(m, o.vi[k], p[0], p[1], p[2]);
+        }
+        o.v[k] = view_space(mv, p);
+    }
     return true;
 }
 

@@ -191,14 +191,21 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
 // memory (queue-1 overflow passes its address on).
 __device__ __forceinline__ void exact_gather(const FrameDev &f, uint2 e, bool live, Tri9 &p) {
     if (live) {
-        const MeshDev *mesh = f.meshes + f.pairs[e.y].mesh;
-        const uint32_t *ix = mesh->idx + 3 * (uint64_t)e.x;
-        const float *pos = mesh->pos;
-        const uint32_t i0 = __ldg(ix), i1 = __ldg(ix + 1), i2 = __ldg(ix + 2);
-        const float *q0 = pos + 3 * (uint64_t)i0, *q1 = pos + 3 * (uint64_t)i1, *q2 = pos + 3 * (uint64_t)i2;
-        p.v[0] = __ldg(q0); p.v[1] = __ldg(q0 + 1); p.v[2] = __ldg(q0 + 2);
-        p.v[3] = __ldg(q1); p.v[4] = __ldg(q1 + 1); p.v[5] = __ldg(q1 + 2);
-        p.v[6] = __ldg(q2); p.v[7] = __ldg(q2 + 1); p.v[8] = __ldg(q2 + 2);
+        const MeshDev &mesh = f.meshes[f.pairs[e.y].mesh];
+        if (!compressed(mesh)) {
+            const uint32_t *ix = mesh.idx + 3 * (uint64_t)e.x;
+            const float *pos = mesh.pos;
+            const uint32_t i0 = __ldg(ix), i1 = __ldg(ix + 1), i2 = __ldg(ix + 2);
+            const float *q0 = pos + 3 * (uint64_t)i0, *q1 = pos + 3 * (uint64_t)i1, *q2 = pos + 3 * (uint64_t)i2;
+            p.v[0] = __ldg(q0); p.v[1] = __ldg(q0 + 1); p.v[2] = __ldg(q0 + 2);
+            p.v[3] = __ldg(q1); p.v[4] = __ldg(q1 + 1); p.v[5] = __ldg(q1 + 2);
+            p.v[6] = __ldg(q2); p.v[7] = __ldg(q2 + 1); p.v[8] = __ldg(q2 + 2);
+        } else {
+            const MeshDev m = mesh;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                mesh_vertex(m, mesh_index(m, 3 * (uint64_t)e.x + c), p.v[3 * c], p.v[3 * c + 1], p.v[3 * c + 2]);
+        }
     } else {
 #pragma unroll
         for (int c = 0; c < 9; ++c) p.v[c] = 0.0f;
@@ -273,7 +280,7 @@ struct Desc {
 
 template <bool INST, bool FUSED>
 struct Smem {
-    uint32_t idx[kSlots][3 * kItem];
+    uint32_t idx[kSlots][3 * kItem + 4];             // index triples, or packed index bits (+1 word read ahead)
     FastPair fp[kSlots][INST ? kMaxPairs : 1];
     MeshDev mesh[kSlots];
     Desc desc[kSlots];
@@ -290,7 +297,7 @@ size_t stage1_smem_bytes() { return sizeof(s1::Smem<INST, FUSED>); }
 // is read one grab ahead), the forward search for the item's segment, the
 // item's pair constants, and the TMA copy of its index triples.  Items
 // [rd.b0, rd.b1) form round r of the frame.
-template <bool INST, bool FUSED>
+template <bool INST, bool FUSED, bool COMP>
 __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST, FUSED> &S, const RoundDev &rd,
                                                 uint32_t r, int n_segs, uint64_t per_item, uint32_t G) {
     using namespace s1;
@@ -366,11 +373,20 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
             fp.lim = make_float4(pr.wsafe, pr.win, (float)(vw.W - 1), (float)(vw.H - 1));
             S.fp[slot][q] = fp;
         }
-        const uint32_t bytes = 12u * d.n;
+        uint32_t bytes = 12u * d.n;
         const uint32_t *src = mesh.idx + 3 * d.t0;
+        if (COMP) {
+            // the item's packed bits start on a word: 3 t0 bits is a multiple
+            // of 32 (t0 is a multiple of 256); one more word is read ahead and
+            // the copy is rounded up to 16 bytes (the packed buffer is padded)
+            const uint64_t w0 = (3 * d.t0 * mesh.bits) >> 5;
+            const uint32_t nw = (uint32_t)((3ull * d.n * mesh.bits + 31) >> 5) + 1;
+            bytes = ((nw + 3u) & ~3u) * 4u;
+            src = mesh.cidx + w0;
+        }
         const bool tma = (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (bytes & 15) == 0;
         if (!tma)
-            for (uint32_t w = lane; w < 3 * d.n; w += 32) S.idx[slot][w] = __ldg(src + w);
+            for (uint32_t w = lane; w < bytes / 4; w += 32) S.idx[slot][w] = __ldg(src + w);
         __syncwarp();
         if (lane == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -392,9 +408,10 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
 // bitmap) queues the survivors per warp and runs the exact path itself,
 // 32 at a time.  INST blocks loop over many pairs (Section 4.5, extended to
 // several views): a triangle's data is loaded once for all of them.
-template <bool INST, bool FUSED>
+template <bool INST, bool FUSED, bool COMP>
 __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
     k_stage1(const __grid_constant__ FrameDev f, uint32_t r) {
+    static_assert(!(FUSED && COMP), "the fused kernel reads uncompressed meshes only");
     using namespace s1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<INST, FUSED> &S = *reinterpret_cast<Smem<INST, FUSED> *>(smem_raw);
@@ -415,7 +432,7 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
     __syncthreads();
 
     if (warp == kConsumerWarps) {
-        stage1_producer<INST, FUSED>(f, S, rd, r, n_segs, per_item, G);
+        stage1_producer<INST, FUSED, COMP>(f, S, rd, r, n_segs, per_item, G);
         return;
     }
 
@@ -438,6 +455,7 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
             // then culled for every pair of the item; the pair constants are
             // read from shared memory, which leaves the registers to the loads
             constexpr int NT = kNT;
+            constexpr bool comp = COMP;                   // rounds hold one kind of mesh
             for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
                 bool valid[NT];
                 uint32_t ix[NT][3];
@@ -447,7 +465,16 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
                     valid[u] = k + u < tpt && lt < d.n;
                     ix[u][0] = ix[u][1] = ix[u][2] = 0;
                     if (valid[u]) {
-                        ix[u][0] = idx[3 * lt]; ix[u][1] = idx[3 * lt + 1]; ix[u][2] = idx[3 * lt + 2];
+                        if (!comp) {
+                            ix[u][0] = idx[3 * lt]; ix[u][1] = idx[3 * lt + 1]; ix[u][2] = idx[3 * lt + 2];
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const uint32_t bit = (3 * lt + c) * mesh.bits;
+                                ix[u][c] = mesh.imin +
+                                           (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
+                            }
+                        }
                         if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= mesh.V) {
                             if (f.check) atomicOr(f.err, kErrIndex);
                             valid[u] = false;
@@ -457,7 +484,10 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
                 Tri9 p[NT];
 #pragma unroll
                 for (int u = 0; u < NT; ++u) {
-                    if (valid[u]) {
+                    if (valid[u] && comp) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) mesh_vertex(mesh, ix[u][c], p[u].v[3 * c], p[u].v[3 * c + 1], p[u].v[3 * c + 2]);
+                    } else if (valid[u]) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const float *q = mesh.pos + 3 * (uint64_t)ix[u][c];

@@ -209,7 +209,7 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     k_static_setup<<<1, 32, 0, s>>>(fr);
     if ((e = cudaGetLastError()) != cudaSuccess) return CURAST_ERR_CUDA;
     if ((e = launch_clear(vis, (uint64_t)W * (uint64_t)H, s)) != cudaSuccess) return CURAST_ERR_CUDA;
-    if ((e = launch_stage1(f, inst, true, 0, sms * ds->shape.stage1_blocks_per_sm[inst ? 1 : 0][1], s)) != cudaSuccess)
+    if ((e = launch_stage1(f, inst, 1, 0, sms * ds->shape.stage1_blocks_per_sm[inst ? 1 : 0][1], s)) != cudaSuccess)
         return CURAST_ERR_CUDA;
     if ((e = launch_stage2(f, sms * ds->shape.stage2_blocks_per_sm, s)) != cudaSuccess) return CURAST_ERR_CUDA;
     if ((e = launch_stage3(f, sms * ds->shape.stage3_blocks_per_sm, s)) != cudaSuccess) return CURAST_ERR_CUDA;
