@@ -47,6 +47,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-supersampling", dest="supersampling", action="store_false",
                    help="skip the 2x2 / 4x4 super-sampled frames")
+    p.add_argument("--no-compressed", dest="compressed", action="store_false",
+                   help="skip the frame with compressed geometry")
     p.add_argument("--subset", type=int, default=0,
                    help="profiling aid: give geometry only to this many tiles next to the view centre "
                         "(same layout, camera and triangle density; the other tiles are empty)")
@@ -363,6 +365,8 @@ def run_ours(args, ranks: Ranks):
     if ranks.rank == 0 and ranks.world == 1 and args.supersampling:
         result["supersampling"] = supersampling(r, cam, args, ms_frame, stream)
     r.close()
+    if ranks.rank == 0 and ranks.world == 1 and args.compressed:
+        result["compressed"] = compressed_frame(args, sc, cam, dev, stream, info, ms_frame)
     del sc, vis
     torch.cuda.empty_cache()
 
@@ -374,6 +378,51 @@ def run_ours(args, ranks: Ranks):
                                   "sample": f"three adjacent central tiles ({n} triangles) of the same frame, "
                                             f"single-threaded oracle, {dt:.1f} s"}
     return result
+
+
+def compressed_frame(args, sc, cam, dev, stream, info_plain, ms_plain):
+    """The same frame with every tile uploaded compressed (Section 4.6):
+    frame and stage times, and the index + position bytes the cull reads."""
+    import torch
+    from paper_2604_21749_gb300 import api
+    r = api.Renderer(dev.index)
+    for m in sc.meshes:
+        r.upload_mesh(m.pos, m.idx, m.rgba8, compressed=True)
+    for it in sc.instances:
+        r.add_instance(it.mesh, it.model)
+    vis = r.new_vis(args.W, args.H)
+    for _ in range(2):
+        r.render(cam.view, cam.proj, args.W, args.H, vis)
+    r.sync()
+    frames = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage = []
+    e0.record(stream)
+    for _ in range(frames):
+        r.render(cam.view, cam.proj, args.W, args.H, vis)
+        stage.append(r.stage_times())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / frames
+    info = r.last_frame()
+    infos = [r.mesh_info(k) for k in range(len(sc.meshes))]
+    bits = [mi["index_bits"] for mi in infos]
+    # the cull reads the visible tiles' packed indices and quantized positions
+    # (the tiles are the same size, one instance each)
+    per_mesh = sum(mi["geometry_bytes"] for mi in infos) / max(len(infos), 1)
+    read_bytes = per_mesh * info["pairs"]
+    plain_bytes = 12.0 * (info_plain["unique_triangles"] + info_plain["unique_vertices"])
+    cull_ms = statistics.mean(s[1] for s in stage)
+    r.close()
+    del vis
+    torch.cuda.empty_cache()
+    return {"frame_ms": round(ms, 4), "vs_uncompressed": round(ms_plain / ms, 3),
+            "stage_ms": {k: round(statistics.mean(s[i] for s in stage), 4)
+                         for i, k in enumerate(["clear", "stage1_cull", "stage1_exact", "stage2", "stage3"])},
+            "index_bits": sorted(set(bits)), "geometry_bytes_read": round(read_bytes),
+            "uncompressed_bytes_read": round(plain_bytes),
+            "cull_gbs": round(read_bytes / (cull_ms * 1e-3) / 1e9, 1),
+            "triangles_per_frame": info["triangles"]}
 
 
 def supersampling(r, cam, args, ms_1x1, stream):
