@@ -184,6 +184,40 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
     cq = sq & (nxq | nyq);
 }
 
+// The same test for a whole group of triangles and one pair, through the
+// eight corners of the group's object-space bounding box, one corner per
+// lane of an aligned group of 8 lanes (all 32 lanes call it).  With every
+// corner in front of the near plane, each vertex of the group projects into
+// the convex hull of the projected corners, so the corners' bbox widened by
+// the bound (doubled: the estimate's error is taken at a corner, the exact
+// path's at a vertex, each bounded at the group's largest 1/w and |X'|)
+// holds every exact snapped vertex of the group.  When it holds no pixel
+// centre, neither does any triangle's.
+__device__ __forceinline__ bool group_cull(const FastPair &fp, float x, float y, float z) {
+    const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw;
+    const float xw = __fmaf_rn(rx.x, x, __fmaf_rn(rx.y, y, __fmaf_rn(rx.z, z, rx.w)));
+    const float yw = __fmaf_rn(ry.x, x, __fmaf_rn(ry.y, y, __fmaf_rn(ry.z, z, ry.w)));
+    float wmn = __fmaf_rn(rw.x, x, __fmaf_rn(rw.y, y, __fmaf_rn(rw.z, z, rw.w)));
+    float rmx = rcp_approx(wmn);
+    float xmn = xw * rmx, xmx = xmn, ymn = yw * rmx, ymx = ymn;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        xmn = fminf(xmn, __shfl_xor_sync(0xffffffffu, xmn, o));
+        xmx = fmaxf(xmx, __shfl_xor_sync(0xffffffffu, xmx, o));
+        ymn = fminf(ymn, __shfl_xor_sync(0xffffffffu, ymn, o));
+        ymx = fmaxf(ymx, __shfl_xor_sync(0xffffffffu, ymx, o));
+        wmn = fminf(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
+        rmx = fmaxf(rmx, __shfl_xor_sync(0xffffffffu, rmx, o));
+    }
+    const float4 k = fp.k, lim = fp.lim;
+    const float a = fmaxf(fmaxf(fabsf(xmn), fabsf(xmx)), fmaxf(fabsf(ymn), fabsf(ymx)));
+    const float m = 2.0f * __fmaf_rn(rmx, __fmaf_rn(k.y, a, k.x), __fmaf_rn(k.z, a, k.w));
+    const bool safe = (wmn > lim.x) & (a < lim.y);
+    const bool nx = floorf(fminf(xmx + m, lim.z)) < fmaxf(xmn - m, 0.0f);
+    const bool ny = floorf(fminf(ymx + m, lim.w)) < fmaxf(ymn - m, 0.0f);
+    return safe & (nx | ny);
+}
+
 // The exact path of one (triangle, pair) that the conservative cull kept:
 // indices and positions from global memory, FP32 transform in the fixed
 // order, clip outcodes, snap, culls, then stage-1 raster or queue 1.
@@ -267,8 +301,10 @@ constexpr int kItem = kConsumers * kMaxTpt;          // 1024 triangles, 12 KB of
 constexpr int kSlots = 3;
 constexpr int kQueue = 64;                           // per-warp survivors (fused kernel)
 constexpr int kMaxPairs = 64;                        // pairs of one segment (pairs_per_segment <= 64)
-constexpr int kNT = 2;                               // triangles a lane loads together (single-pair items)
-constexpr int kCullBlocks = 4;                       // cull blocks per SM: 56 registers a thread
+constexpr int kNT = 2;                               // triangles a lane loads together
+constexpr uint32_t kGroupMinPairs = 2;               // items with this many pairs test groups first
+constexpr int kCullBlocks = 4;                       // single-pair cull blocks per SM: 56 registers a thread
+                                                     // (instanced and fused: 3, 72 registers)
 
 struct Desc {
     unsigned long long b;  // work item, >= the round's end: none (consumers stop)
@@ -409,7 +445,7 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
 // 32 at a time.  INST blocks loop over many pairs (Section 4.5, extended to
 // several views): a triangle's data is loaded once for all of them.
 template <bool INST, bool FUSED, bool COMP>
-__global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
+__global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullBlocks)
     k_stage1(const __grid_constant__ FrameDev f, uint32_t r) {
     static_assert(!(FUSED && COMP), "the fused kernel reads uncompressed meshes only");
     using namespace s1;
@@ -456,58 +492,176 @@ __global__ void __launch_bounds__(s1::kThreads, FUSED ? 3 : s1::kCullBlocks)
             // read from shared memory, which leaves the registers to the loads
             constexpr int NT = kNT;
             constexpr bool comp = COMP;                   // rounds hold one kind of mesh
-            for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
-                bool valid[NT];
-                uint32_t ix[NT][3];
-#pragma unroll
-                for (int u = 0; u < NT; ++u) {
-                    const uint32_t lt = (k + u) * kConsumers + tid;
-                    valid[u] = k + u < tpt && lt < d.n;
-                    ix[u][0] = ix[u][1] = ix[u][2] = 0;
-                    if (valid[u]) {
-                        if (!comp) {
-                            ix[u][0] = idx[3 * lt]; ix[u][1] = idx[3 * lt + 1]; ix[u][2] = idx[3 * lt + 2];
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const uint32_t bit = (3 * lt + c) * mesh.bits;
-                                ix[u][c] = mesh.imin +
-                                           (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
-                            }
-                        }
-                        if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= mesh.V) {
-                            if (f.check) atomicOr(f.err, kErrIndex);
-                            valid[u] = false;
-                        }
-                    }
-                }
-                Tri9 p[NT];
-#pragma unroll
-                for (int u = 0; u < NT; ++u) {
-                    if (valid[u] && comp) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) mesh_vertex(mesh, ix[u][c], p[u].v[3 * c], p[u].v[3 * c + 1], p[u].v[3 * c + 2]);
-                    } else if (valid[u]) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float *q = mesh.pos + 3 * (uint64_t)ix[u][c];
-                            p[u].v[3 * c] = __ldg(q); p[u].v[3 * c + 1] = __ldg(q + 1); p[u].v[3 * c + 2] = __ldg(q + 2);
-                        }
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
-                    }
-                }
-                for (uint32_t pi = 0; pi < np; ++pi) {
-                    bool cull[NT];
-                    static_assert(NT == 2, "the cull evaluates triangles in packed pairs");
-                    fast_cull2(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
+            if constexpr (!INST) {
+                for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
+                    bool valid[NT];
+                    uint32_t ix[NT][3];
 #pragma unroll
                     for (int u = 0; u < NT; ++u) {
-                        const bool live = valid[u] && !cull[u];
-                        if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
-                        const unsigned m = __ballot_sync(0xffffffffu, live);
-                        if (k + u < tpt && lane == 0) f.bits[d.wbase + pi * G + (k + u) * kConsumerWarps + warp] = m;
+                        const uint32_t lt = (k + u) * kConsumers + tid;
+                        valid[u] = k + u < tpt && lt < d.n;
+                        ix[u][0] = ix[u][1] = ix[u][2] = 0;
+                        if (valid[u]) {
+                            if (!comp) {
+                                ix[u][0] = idx[3 * lt]; ix[u][1] = idx[3 * lt + 1]; ix[u][2] = idx[3 * lt + 2];
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    const uint32_t bit = (3 * lt + c) * mesh.bits;
+                                    ix[u][c] = mesh.imin +
+                                               (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
+                                }
+                            }
+                            if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= mesh.V) {
+                                if (f.check) atomicOr(f.err, kErrIndex);
+                                valid[u] = false;
+                            }
+                        }
+                    }
+                    Tri9 p[NT];
+#pragma unroll
+                    for (int u = 0; u < NT; ++u) {
+                        if (valid[u] && comp) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) mesh_vertex(mesh, ix[u][c], p[u].v[3 * c], p[u].v[3 * c + 1], p[u].v[3 * c + 2]);
+                        } else if (valid[u]) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const float *q = mesh.pos + 3 * (uint64_t)ix[u][c];
+                                p[u].v[3 * c] = __ldg(q); p[u].v[3 * c + 1] = __ldg(q + 1); p[u].v[3 * c + 2] = __ldg(q + 2);
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
+                        }
+                    }
+                    for (uint32_t pi = 0; pi < np; ++pi) {
+                        bool cull[NT];
+                        static_assert(NT == 2, "the cull evaluates triangles in packed pairs");
+                        fast_cull2(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
+#pragma unroll
+                        for (int u = 0; u < NT; ++u) {
+                            const bool live = valid[u] && !cull[u];
+                            if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
+                            const unsigned m = __ballot_sync(0xffffffffu, live);
+                            if (k + u < tpt && lane == 0) f.bits[d.wbase + pi * G + (k + u) * kConsumerWarps + warp] = m;
+                        }
+                    }
+                }
+            } else {
+                // A lane takes one triangle of each of nv 32-triangle runs a
+                // step; the warp's ballot over run q is bitmap word q of the
+                // pair.  Single-pair items take runs (k + u) * 8 + warp; the
+                // instanced ones, whose group test wants the step's triangles
+                // together, the adjacent runs k * 8 + nv * warp + u.
+                for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
+                    bool valid[NT];
+                    uint32_t ix[NT][3];
+#pragma unroll
+                    for (int u = 0; u < NT; ++u) {
+                        const uint32_t lt = 32 * (k * kConsumerWarps + min((uint32_t)NT, tpt - k) * warp + u) + lane;
+                        valid[u] = k + u < tpt && lt < d.n;
+                        ix[u][0] = ix[u][1] = ix[u][2] = 0;
+                        if (valid[u]) {
+                            if (!comp) {
+                                ix[u][0] = idx[3 * lt]; ix[u][1] = idx[3 * lt + 1]; ix[u][2] = idx[3 * lt + 2];
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    const uint32_t bit = (3 * lt + c) * mesh.bits;
+                                    ix[u][c] = mesh.imin +
+                                               (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
+                                }
+                            }
+                            if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= mesh.V) {
+                                if (f.check) atomicOr(f.err, kErrIndex);
+                                valid[u] = false;
+                            }
+                        }
+                    }
+                    Tri9 p[NT];
+#pragma unroll
+                    for (int u = 0; u < NT; ++u) {
+                        if (valid[u] && comp) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) mesh_vertex(mesh, ix[u][c], p[u].v[3 * c], p[u].v[3 * c + 1], p[u].v[3 * c + 2]);
+                        } else if (valid[u]) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const float *q = mesh.pos + 3 * (uint64_t)ix[u][c];
+                                p[u].v[3 * c] = __ldg(q); p[u].v[3 * c + 1] = __ldg(q + 1); p[u].v[3 * c + 2] = __ldg(q + 2);
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
+                        }
+                    }
+                    static_assert(NT == 2, "the cull evaluates triangles in packed pairs");
+                    if (np >= kGroupMinPairs) {
+                        const uint32_t nv = min((uint32_t)NT, tpt - k);
+                        const uint32_t run0 = k * kConsumerWarps + nv * warp;
+                        // Instanced items first test the step's triangles as one
+                        // group per pair, four pairs at a time (8 lanes a pair, one
+                        // bbox corner a lane); the rejected pairs get zero words in
+                        // bulk and only the others run the per-triangle test.
+                        float gc[3];                       // this lane's corner of the group's bbox
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+                            for (int u = 0; u < NT; ++u)
+                                if (valid[u])
+#pragma unroll
+                                    for (int c = 0; c < 3; ++c) lo = fminf(lo, p[u].v[3 * c + a]), hi = fmaxf(hi, p[u].v[3 * c + a]);
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+                                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                            }
+                            gc[a] = (lane >> a) & 1 ? hi : lo;
+                        }
+                        uint64_t keep = 0;                 // pairs whose group test failed
+                        for (uint32_t pb = 0; pb < np; pb += 4) {
+                            const uint32_t q = pb + (lane >> 3);
+                            const bool g = group_cull(S.fp[slot][min(q, np - 1)], gc[0], gc[1], gc[2]);
+                            const unsigned b = __ballot_sync(0xffffffffu, !g && (lane & 7) == 0 && q < np);
+                            keep |= (uint64_t)((b & 1u) | ((b >> 7) & 2u) | ((b >> 14) & 4u) | ((b >> 21) & 8u)) << pb;
+                        }
+                        for (uint32_t i0 = 0; i0 < 2 * np; i0 += 32) {
+                            const uint32_t i = i0 + lane, pi = i >> 1, u = i & 1u;
+                            if (i < 2 * np && u < nv && !((keep >> pi) & 1u)) f.bits[d.wbase + pi * G + run0 + u] = 0u;
+                        }
+                        if (f.stats) {
+                            const uint32_t rejected = np - (uint32_t)__popcll(keep);
+                            const uint32_t nvalid = (uint32_t)valid[0] + (uint32_t)valid[1];
+                            if (rejected && nvalid) stat_add(f, kStatIn, rejected * nvalid), stat_add(f, kStatTiny, rejected * nvalid);
+                        }
+                        while (keep) {
+                            const uint32_t pi = (uint32_t)__ffsll((long long)keep) - 1;
+                            keep &= keep - 1;
+                            bool cull[NT];
+                            fast_cull2(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
+#pragma unroll
+                            for (int u = 0; u < NT; ++u) {
+                                const bool live = valid[u] && !cull[u];
+                                if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
+                                const unsigned m = __ballot_sync(0xffffffffu, live);
+                                if (u < nv && lane == 0) f.bits[d.wbase + pi * G + run0 + u] = m;
+                            }
+                        }
+                    } else {
+                        for (uint32_t pi = 0; pi < np; ++pi) {
+                            bool cull[NT];
+                            fast_cull2(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
+#pragma unroll
+                            for (int u = 0; u < NT; ++u) {
+                                const bool live = valid[u] && !cull[u];
+                                if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
+                                const unsigned m = __ballot_sync(0xffffffffu, live);
+                                const uint32_t word = k * kConsumerWarps + min((uint32_t)NT, tpt - k) * warp + u;
+                                if (k + u < tpt && lane == 0) f.bits[d.wbase + pi * G + word] = m;
+                            }
+                        }
                     }
                 }
             }

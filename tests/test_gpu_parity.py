@@ -142,6 +142,31 @@ def test_batched_views_equal_oracle(api, mixed, use_graph, bitmap):
     del keep
 
 
+@pytest.fixture(scope="module")
+def many_small():
+    """The many-mesh workload's structure scaled down: 16 meshes of 2e3..5e4
+    triangles, 200 randomly rotated instances of scale 0.1..10 over a
+    200 x 200 area, two views; most instances cover a few pixels, so many of
+    the instanced cull's groups hold no pixel centre and the rest do."""
+    return S.scene_batched(n_meshes=16, n_instances=200, tmin=2e3, tmax=5e4,
+                           views=((640, 360), (320, 180)), seed=31)
+
+
+@pytest.mark.parametrize("pps", [1, 3, 64])
+def test_many_small_instances_equal_oracle(api, many_small, pps):
+    """Instanced items test each step's triangles per pair as a group first
+    (one to 64 pairs an item); the buffers stay identical to the oracle's."""
+    r = _renderer(api, pairs_per_segment=pps, collect_stats=1)
+    keep = upload(r, many_small, with_colour=False)
+    views = [(c.view, c.proj, c.W, c.H, None) for c in many_small.cameras]
+    out = r.render_batch(views, use_graph=False)
+    st = r.sync()
+    for c, v in zip(many_small.cameras, out):
+        assert_vis_equal(v, oracle_vis(many_small, c), f"many small instances {c.W}x{c.H} pps {pps}")
+    assert st["culled_tiny"] > 0 and st["stage1_rasterized"] > 0
+    del keep
+
+
 def test_per_mesh_launches_equal_oracle(api, mixed):
     """The one-launch-per-mesh-per-view path composes to the same buffer."""
     r = _renderer(api)
