@@ -38,6 +38,9 @@ struct PairDev {             // one (instance, view) pair that survived host cul
     float fn[12];
     float fk[4];
     float wsafe, win;
+    // bound on the rounding of a row evaluated anywhere in the mesh bounds,
+    // for the X'*w, Y'*w and w rows (2^-19 times the row's magnitude bound)
+    float fs[3], pad;
     uint64_t base;           // global id of the instance's triangle 0
     uint32_t view;
     uint32_t mesh;

@@ -154,6 +154,8 @@ bool instance_visible(const float *mv, const MeshRec &m, const Cam &cam) {
 void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     std::memset(p.fn, 0, sizeof(p.fn));
     std::memset(p.fk, 0, sizeof(p.fk));
+    std::memset(p.fs, 0, sizeof(p.fs));
+    p.pad = 0.0f;
     p.wsafe = INFINITY;
     p.win = 0.0f;
     if (!m.bounded) return;
@@ -199,6 +201,12 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     p.fk[1] = (float)(kb * (1 + 1e-6));
     p.fk[2] = (float)(kc * (1 + 1e-6));
     p.fk[3] = (float)(kd * (1 + 1e-6));
+    // the rows' magnitude over the mesh bounds is at most ax S_0 + bx S_2,
+    // ay S_1 + by S_2 and S_2; 2^-19 of it covers the rounding of the group
+    // test's box arithmetic (centre, half extent, row sums: a few u each)
+    p.fs[0] = (float)(std::ldexp(ax * S[0] + bx * S[2], -19) * (1 + 1e-6));
+    p.fs[1] = (float)(std::ldexp(ay * S[1] + by * S[2], -19) * (1 + 1e-6));
+    p.fs[2] = (float)(std::ldexp(S[2], -19) * (1 + 1e-6));
     p.wsafe = (float)(ws * (1 + 1e-6));
     // inside |X'|, |Y'| < 8 min(W/2, H/2) every vertex lies far within the
     // guard band (|X - W/2| <= 128 W/2, likewise for Y), so the exact path

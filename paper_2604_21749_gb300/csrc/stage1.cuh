@@ -69,6 +69,7 @@ struct __align__(16) FastPair {
     float4 k;                   // ka, kb, kc, kd
     float4 lim;                 // wsafe, win, W - 1, H - 1 (every w > wsafe and |X'|, |Y'| < win;
                                 // the last pixel centre)
+    float4 sl;                  // rounding bound of the rows over the mesh bounds (group test), 0
 };
 
 struct Tri9 { float v[9]; };    // the three vertices of a triangle
@@ -184,37 +185,42 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
     cq = sq & (nxq | nyq);
 }
 
-// The same test for a whole group of triangles and one pair, through the
-// eight corners of the group's object-space bounding box, one corner per
-// lane of an aligned group of 8 lanes (all 32 lanes call it).  With every
-// corner in front of the near plane, each vertex of the group projects into
-// the convex hull of the projected corners, so the corners' bbox widened by
-// the bound (doubled: the estimate's error is taken at a corner, the exact
-// path's at a vertex, each bounded at the group's largest 1/w and |X'|)
-// holds every exact snapped vertex of the group.  When it holds no pixel
-// centre, neither does any triangle's.
-__device__ __forceinline__ bool group_cull(const FastPair &fp, float x, float y, float z) {
-    const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw;
-    const float xw = __fmaf_rn(rx.x, x, __fmaf_rn(rx.y, y, __fmaf_rn(rx.z, z, rx.w)));
-    const float yw = __fmaf_rn(ry.x, x, __fmaf_rn(ry.y, y, __fmaf_rn(ry.z, z, ry.w)));
-    float wmn = __fmaf_rn(rw.x, x, __fmaf_rn(rw.y, y, __fmaf_rn(rw.z, z, rw.w)));
-    float rmx = rcp_approx(wmn);
-    float xmn = xw * rmx, xmx = xmn, ymn = yw * rmx, ymx = ymn;
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        xmn = fminf(xmn, __shfl_xor_sync(0xffffffffu, xmn, o));
-        xmx = fmaxf(xmx, __shfl_xor_sync(0xffffffffu, xmx, o));
-        ymn = fminf(ymn, __shfl_xor_sync(0xffffffffu, ymn, o));
-        ymx = fmaxf(ymx, __shfl_xor_sync(0xffffffffu, ymx, o));
-        wmn = fminf(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
-        rmx = fmaxf(rmx, __shfl_xor_sync(0xffffffffu, rmx, o));
-    }
+// The same test for a whole group of triangles and one pair, from the
+// group's object-space bounding box (centre c, half extent e).  With
+// X0 = (X' w)(c) / w(c) the projected centre, X' = X0 + d / w where
+// d = X' w - X0 w is affine in the position; over the box |d| is at most its
+// value at c plus the |coefficient|-weighted extent, and w is at least
+// w(c) less its own weighted extent (each widened by the rows' rounding
+// bound).  So, with every w above wsafe, X' lies within X0 +- max|d| / min w
+// for every vertex of the group, and the margin (doubled: the range and the
+// exact snapped vertices each take their error at the group's largest 1/w
+// and |X'|) holds every exact snapped vertex.  When the widened ranges hold
+// no pixel centre, no triangle's bbox does.
+__device__ __forceinline__ bool group_cull(const FastPair &fp, float3 c, float3 e) {
+    const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw, sl = fp.sl;
+    const float cx = __fmaf_rn(rx.x, c.x, __fmaf_rn(rx.y, c.y, __fmaf_rn(rx.z, c.z, rx.w)));
+    const float cy = __fmaf_rn(ry.x, c.x, __fmaf_rn(ry.y, c.y, __fmaf_rn(ry.z, c.z, ry.w)));
+    const float cw = __fmaf_rn(rw.x, c.x, __fmaf_rn(rw.y, c.y, __fmaf_rn(rw.z, c.z, rw.w)));
+    const float ew = __fmaf_rn(fabsf(rw.x), e.x, __fmaf_rn(fabsf(rw.y), e.y, __fmaf_rn(fabsf(rw.z), e.z, sl.z)));
+    const float wl = cw - ew;
+    const float r0 = rcp_approx(cw);
+    const float X0 = cx * r0, Y0 = cy * r0;
+    const float dx = __fmaf_rn(fabsf(__fmaf_rn(-X0, rw.x, rx.x)), e.x,
+                     __fmaf_rn(fabsf(__fmaf_rn(-X0, rw.y, rx.y)), e.y,
+                     __fmaf_rn(fabsf(__fmaf_rn(-X0, rw.z, rx.z)), e.z,
+                     __fmaf_rn(fabsf(X0), sl.z, fabsf(__fmaf_rn(-X0, cw, cx)) + sl.x))));
+    const float dy = __fmaf_rn(fabsf(__fmaf_rn(-Y0, rw.x, ry.x)), e.x,
+                     __fmaf_rn(fabsf(__fmaf_rn(-Y0, rw.y, ry.y)), e.y,
+                     __fmaf_rn(fabsf(__fmaf_rn(-Y0, rw.z, ry.z)), e.z,
+                     __fmaf_rn(fabsf(Y0), sl.z, fabsf(__fmaf_rn(-Y0, cw, cy)) + sl.y))));
+    const float rh = rcp_approx(wl) * 1.0000039f;           // >= 1/w over the box (2^-18 over rcp's error)
+    const float hx = dx * rh, hy = dy * rh;
     const float4 k = fp.k, lim = fp.lim;
-    const float a = fmaxf(fmaxf(fabsf(xmn), fabsf(xmx)), fmaxf(fabsf(ymn), fabsf(ymx)));
-    const float m = 2.0f * __fmaf_rn(rmx, __fmaf_rn(k.y, a, k.x), __fmaf_rn(k.z, a, k.w));
-    const bool safe = (wmn > lim.x) & (a < lim.y);
-    const bool nx = floorf(fminf(xmx + m, lim.z)) < fmaxf(xmn - m, 0.0f);
-    const bool ny = floorf(fminf(ymx + m, lim.w)) < fmaxf(ymn - m, 0.0f);
+    const float a = fmaxf(fabsf(X0) + hx, fabsf(Y0) + hy);
+    const float m = 2.0f * __fmaf_rn(rh, __fmaf_rn(k.y, a, k.x), __fmaf_rn(k.z, a, k.w)) + 2.0f * (hx + hy) * 4.0e-6f;
+    const bool safe = (wl > lim.x) & (a < lim.y);
+    const bool nx = floorf(fminf(X0 + hx + m, lim.z)) < fmaxf(X0 - hx - m, 0.0f);
+    const bool ny = floorf(fminf(Y0 + hy + m, lim.w)) < fmaxf(Y0 - hy - m, 0.0f);
     return safe & (nx | ny);
 }
 
@@ -407,6 +413,7 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
             fp.rw = make_float4(pr.fn[8], pr.fn[9], pr.fn[10], pr.fn[11]);
             fp.k = make_float4(pr.fk[0], pr.fk[1], pr.fk[2], pr.fk[3]);
             fp.lim = make_float4(pr.wsafe, pr.win, (float)(vw.W - 1), (float)(vw.H - 1));
+            fp.sl = make_float4(pr.fs[0], pr.fs[1], pr.fs[2], 0.0f);
             S.fp[slot][q] = fp;
         }
         uint32_t bytes = 12u * d.n;
@@ -601,31 +608,36 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
                         const uint32_t nv = min((uint32_t)NT, tpt - k);
                         const uint32_t run0 = k * kConsumerWarps + nv * warp;
                         // Instanced items first test the step's triangles as one
-                        // group per pair, four pairs at a time (8 lanes a pair, one
-                        // bbox corner a lane); the rejected pairs get zero words in
-                        // bulk and only the others run the per-triangle test.
-                        float gc[3];                       // this lane's corner of the group's bbox
+                        // group per pair, one pair a lane; the rejected pairs get
+                        // zero words in bulk and only the others run the
+                        // per-triangle test.
+                        float3 gc, ge;                     // the group's box: centre, half extent
+                        {
+                            float lo[3], hi[3];
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            float lo = INFINITY, hi = -INFINITY;
+                            for (int a = 0; a < 3; ++a) {
+                                lo[a] = INFINITY, hi[a] = -INFINITY;
 #pragma unroll
-                            for (int u = 0; u < NT; ++u)
-                                if (valid[u])
+                                for (int u = 0; u < NT; ++u)
+                                    if (valid[u])
 #pragma unroll
-                                    for (int c = 0; c < 3; ++c) lo = fminf(lo, p[u].v[3 * c + a]), hi = fmaxf(hi, p[u].v[3 * c + a]);
+                                        for (int c = 0; c < 3; ++c)
+                                            lo[a] = fminf(lo[a], p[u].v[3 * c + a]), hi[a] = fmaxf(hi[a], p[u].v[3 * c + a]);
 #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                                for (int o = 16; o > 0; o >>= 1) {
+                                    lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+                                    hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+                                }
                             }
-                            gc[a] = (lane >> a) & 1 ? hi : lo;
+                            gc = make_float3(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]));
+                            ge = make_float3(fmaxf(hi[0] - gc.x, gc.x - lo[0]), fmaxf(hi[1] - gc.y, gc.y - lo[1]),
+                                             fmaxf(hi[2] - gc.z, gc.z - lo[2]));
                         }
                         uint64_t keep = 0;                 // pairs whose group test failed
-                        for (uint32_t pb = 0; pb < np; pb += 4) {
-                            const uint32_t q = pb + (lane >> 3);
-                            const bool g = group_cull(S.fp[slot][min(q, np - 1)], gc[0], gc[1], gc[2]);
-                            const unsigned b = __ballot_sync(0xffffffffu, !g && (lane & 7) == 0 && q < np);
-                            keep |= (uint64_t)((b & 1u) | ((b >> 7) & 2u) | ((b >> 14) & 4u) | ((b >> 21) & 8u)) << pb;
+                        for (uint32_t pb = 0; pb < np; pb += 32) {
+                            const uint32_t q = pb + lane;
+                            const bool g = q < np && group_cull(S.fp[slot][q < np ? q : 0], gc, ge);
+                            keep |= (uint64_t)__ballot_sync(0xffffffffu, q < np && !g) << pb;
                         }
                         for (uint32_t i0 = 0; i0 < 2 * np; i0 += 32) {
                             const uint32_t i = i0 + lane, pi = i >> 1, u = i & 1u;

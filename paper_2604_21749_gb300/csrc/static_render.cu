@@ -62,6 +62,8 @@ __global__ void k_static_setup(StaticFrame s) {
         for (int q = 0; q < 12; ++q) p.mv[q] = s.mv[t][q];
         for (int q = 0; q < 12; ++q) p.fn[q] = 0.0f;
         for (int q = 0; q < 4; ++q) p.fk[q] = 0.0f;
+        for (int q = 0; q < 3; ++q) p.fs[q] = 0.0f;
+        p.pad = 0.0f;
         p.wsafe = INFINITY;   // no conservative cull: every triangle takes the exact path
         p.win = 0.0f;
         p.base = s.base[t];
