@@ -733,17 +733,19 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
 // and the set bits are compacted into a shared-memory batch of up to
 // 32 * kExactK survivors.  A full batch is gathered at once (every lane
 // issues the index and position loads of its kExactK survivors before any
-// arithmetic) and then run through the exact path.
+// arithmetic), parked in shared memory, and run through the exact path one
+// survivor a lane at a time.
 namespace s1 {
 constexpr int kExactWarps = 4;
-constexpr int kExactBlocks = 4;                      // 128 registers a thread
-constexpr int kExactK = 2;                           // survivors a lane gathers together
+constexpr int kExactBlocks = 5;                      // 96 registers a thread
+constexpr int kExactK = 3;                           // survivors a lane gathers together
 constexpr int kBatch = 32 * kExactK;
 }
 __global__ void __launch_bounds__(32 * s1::kExactWarps, s1::kExactBlocks)
     k_stage1_exact(const __grid_constant__ FrameDev f, uint32_t r) {
     using namespace s1;
     __shared__ uint2 buf[kExactWarps][kBatch];
+    __shared__ float stage[kExactWarps][kExactK][9][32];   // gathered positions, lane-minor
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RoundDev rd = f.rounds[r];
     const uint64_t nwords = rd.w1 - rd.w0;
@@ -816,9 +818,20 @@ __global__ void __launch_bounds__(32 * s1::kExactWarps, s1::kExactBlocks)
         }
 #pragma unroll
         for (int u = 0; u < kExactK; ++u) exact_gather(f, e[u], live[u], p[u]);
-        __syncwarp();
+        // the positions wait in shared memory, so the exact path of one
+        // survivor holds no registers for the others
 #pragma unroll
         for (int u = 0; u < kExactK; ++u)
-            if (__any_sync(0xffffffffu, live[u])) exact_compute(f, e[u], live[u], p[u]);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) stage[warp][u][c][lane] = p[u].v[c];
+        __syncwarp();
+#pragma unroll 1
+        for (int u = 0; u < kExactK; ++u) {
+            if (!__any_sync(0xffffffffu, live[u])) continue;
+            Tri9 q;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) q.v[c] = stage[warp][u][c][lane];
+            exact_compute(f, buf[warp][live[u] ? lane + 32 * u : 0], live[u], q);
+        }
     }
 }
