@@ -89,6 +89,11 @@ typedef struct {
     uint64_t stage1_bitmap_bytes; /* survivor bitmap of the stage-1 cull (1 bit per triangle x
                                     pair); a frame needing more runs stage 1 in several
                                     rounds, 2^12..2^36                                       */
+    uint32_t stage1_group_min_pairs; /* work items with at least this many (instance, view)
+                                    pairs test each step's 64 triangles as one box per pair
+                                    before the per-triangle cull (default 2); 0 turns the
+                                    group test off, 0..64                                    */
+    uint32_t reserved;           /* 0                                                        */
 } curast_config;
 
 /* Counters read back by curast_sync.  Stats fields are filled only when

@@ -154,6 +154,7 @@ struct FrameDev {
     uint32_t tpt;            // stage-1 triangles per thread per grab
     uint32_t check;          // bounds-check indices
     uint32_t stats;          // count statistics
+    uint32_t group_min;      // instanced items with >= this many pairs (> 0) run the group test
 };
 
 constexpr unsigned kErrIndex = 1u;     // a vertex index >= V was skipped

@@ -227,6 +227,7 @@ curast_config default_config() {
     c.queue1_capacity = 1ull << 22;
     c.queue2_capacity = 1ull << 21;
     c.stage1_bitmap_bytes = 1ull << 32;
+    c.stage1_group_min_pairs = 2;
     c.check_indices = 1;
     c.collect_stats = 0;
     return c;
@@ -547,6 +548,7 @@ FrameDev make_frame_dev(const curast_ctx *c) {
     f.s2_max = c->cfg.stage2_max_pixels;
     f.tile_log2 = c->cfg.tile_log2;
     f.tpt = c->cfg.stage1_tri_per_thread;
+    f.group_min = c->cfg.stage1_group_min_pairs;
     f.check = c->cfg.check_indices;
     f.stats = c->cfg.collect_stats;
     return f;
@@ -758,7 +760,8 @@ bool valid_config(const curast_config &c) {
            c.tile_log2 >= 4 && c.tile_log2 <= 7 && c.stage1_tri_per_thread >= 1 && c.stage1_tri_per_thread <= 4 &&
            c.pairs_per_segment >= 1 && c.pairs_per_segment <= 64 && c.queue1_capacity >= 1 &&
            c.queue2_capacity >= 1 && c.queue1_capacity <= (1ull << 32) && c.queue2_capacity <= (1ull << 32) &&
-           c.stage1_bitmap_bytes >= (1ull << 12) && c.stage1_bitmap_bytes <= (1ull << 36);
+           c.stage1_bitmap_bytes >= (1ull << 12) && c.stage1_bitmap_bytes <= (1ull << 36) &&
+           c.stage1_group_min_pairs <= 64 && c.reserved == 0;
 }
 
 }  // namespace

@@ -308,7 +308,6 @@ constexpr int kSlots = 3;
 constexpr int kQueue = 64;                           // per-warp survivors (fused kernel)
 constexpr int kMaxPairs = 64;                        // pairs of one segment (pairs_per_segment <= 64)
 constexpr int kNT = 2;                               // triangles a lane loads together
-constexpr uint32_t kGroupMinPairs = 2;               // items with this many pairs test groups first
 constexpr int kCullBlocks = 4;                       // single-pair cull blocks per SM: 56 registers a thread
                                                      // (instanced and fused: 3, 72 registers)
 
@@ -604,7 +603,7 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
                         }
                     }
                     static_assert(NT == 2, "the cull evaluates triangles in packed pairs");
-                    if (np >= kGroupMinPairs) {
+                    if (f.group_min != 0 && np >= f.group_min) {
                         const uint32_t nv = min((uint32_t)NT, tpt - k);
                         const uint32_t run0 = k * kConsumerWarps + nv * warp;
                         // Instanced items first test the step's triangles as one

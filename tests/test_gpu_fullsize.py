@@ -118,15 +118,24 @@ def _batched_renderer(api, sc):
 
 
 def test_batched_full_size_equals_per_mesh_launches(api):
-    """At full size: the batched launch (replayed from a CUDA graph) and one
-    launch per mesh per view give identical buffers, and every sampled
-    winning fragment is the oracle's fragment of that triangle there."""
+    """At full size: the batched launch (replayed from a CUDA graph), the same
+    launch without the instanced group test, and one launch per mesh per view
+    give identical buffers, and every sampled winning fragment is the
+    oracle's fragment of that triangle there."""
     sc = S.scene_batched(device="cuda")
     r = _batched_renderer(api, sc)
     views = [(c.view, c.proj, c.W, c.H, None) for c in sc.cameras]
     out = r.render_batch(views, use_graph=True)
     out = r.render_batch(views, use_graph=True)     # second frame: graph replay
     r.sync()
+    cfg = r.config
+    r.set_config(stage1_group_min_pairs=0)
+    no_group = r.render_batch(views, use_graph=False)
+    r.sync()
+    for v, w in zip(out, no_group):
+        assert torch.equal(v, w), "the group test changed a visibility buffer"
+    del no_group
+    r.set_config(stage1_group_min_pairs=cfg.stage1_group_min_pairs)
     for c, v in zip(sc.cameras, out):
         plain = r.new_vis(c.W, c.H)
         r.clear(plain)

@@ -152,11 +152,12 @@ def many_small():
                            views=((640, 360), (320, 180)), seed=31)
 
 
-@pytest.mark.parametrize("pps", [1, 3, 64])
-def test_many_small_instances_equal_oracle(api, many_small, pps):
+@pytest.mark.parametrize("pps,group_min", [(1, 2), (3, 2), (64, 2), (64, 1), (64, 0)])
+def test_many_small_instances_equal_oracle(api, many_small, pps, group_min):
     """Instanced items test each step's triangles per pair as a group first
-    (one to 64 pairs an item); the buffers stay identical to the oracle's."""
-    r = _renderer(api, pairs_per_segment=pps, collect_stats=1)
+    (one to 64 pairs an item; from 1 or 2 pairs, or never); the buffers stay
+    identical to the oracle's."""
+    r = _renderer(api, pairs_per_segment=pps, collect_stats=1, stage1_group_min_pairs=group_min)
     keep = upload(r, many_small, with_colour=False)
     views = [(c.view, c.proj, c.W, c.H, None) for c in many_small.cameras]
     out = r.render_batch(views, use_graph=False)
@@ -257,6 +258,8 @@ def test_invalid_arguments_rejected(api):
         r.render(v, cam.proj, 8, 8)
     with pytest.raises(api.CurastError):
         r.set_config(tile_log2=9)
+    with pytest.raises(api.CurastError):
+        r.set_config(stage1_group_min_pairs=65)
 
 
 def test_autotune_keeps_result(api, mixed):
