@@ -38,7 +38,8 @@
  *      interpolate from the inside vertex towards the outside vertex, which
  *      makes shared edges clip identically in both triangles (watertight);
  *   R4 one coverage rule for every triangle size (the paper's stage-3 world
- *      space ray cast is replaced by the same fixed-point rule);
+ *      space ray cast is replaced by the same fixed-point rule); the ray
+ *      cast itself is orc_render_paper at the end of this file (R16);
  *   R5 ids are numbered over all instances, culled or not;
  *   R6 ties in depth28 go to the smaller id (64-bit minimum).
  *
@@ -662,6 +663,173 @@ int orc_interpolate(const orc_mesh *meshes, int n_meshes, const orc_instance *in
                                                           attr[(uint64_t)C * vi[2] + ch]) : 0.0f;
             if (bary) { bary[3 * pix] = b[0]; bary[3 * pix + 1] = b[1]; bary[3 * pix + 2] = b[2]; }
         }
+    free(base);
+    return ORC_OK;
+}
+
+/* ------------------------------------------- paper-faithful stage 3 */
+
+/* Bit p set when clip-space vertex v lies outside plane p (0 near, 1..4 the
+ * guard band), NaN counting as outside. */
+static unsigned outcode5(orc_cv v, float nearv)
+{
+    unsigned o = 0;
+    for (int p = 0; p < 5; ++p)
+        if (!(plane_value(p, v, nearv) >= 0.0f)) o |= 1u << p;
+    return o;
+}
+
+/* Pixel centres covered by the snapped range [mn, mx] (1/256 px), clamped
+ * to [0, n - 1]; lo > hi when there are none. */
+static void centre_range(int64_t mn, int64_t mx, int n, int64_t *lo, int64_t *hi)
+{
+    *lo = ceil_div256(mn - 128);
+    *hi = floor_div256(mx - 128);
+    if (*lo < 0) *lo = 0;
+    if (*hi > n - 1) *hi = n - 1;
+}
+
+/* Section 4.3 as the paper describes it: the large-triangle stage casts, for
+ * every pixel centre of the triangle's visible bbox, a ray from the camera
+ * in view space (camera at the origin) and intersects it with the triangle.
+ * r = (ndx / fx, ndy / fy, -1) with ndx = (2x + 1) / W - 1; with
+ * e1 = v1 - v0, e2 = v2 - v0, p = r x e2, det = e1.p, u = (-v0).p / det,
+ * q = (-v0) x e1, w = r.q / det, b0 = (1 - u) - w and t = e2.q / det, the
+ * pixel is covered when det > 0 (the front side faces the camera), u, w and
+ * b0 are >= 0 and t >= near; its depth is t, the view-space distance along
+ * -z that the edge-function depth of Eq. 2 also gives. */
+static void raycast_range(const float v[3][3], float fx, float fy, float nearv, int W, int H, int64_t x0,
+                          int64_t x1, int64_t y0, int64_t y1, uint64_t id, uint64_t *vis)
+{
+    float e1[3], e2[3], tv[3], qv[3];
+    for (int k = 0; k < 3; ++k) { e1[k] = v[1][k] - v[0][k]; e2[k] = v[2][k] - v[0][k]; tv[k] = -v[0][k]; }
+    cross3(tv, e1, qv);
+    for (int64_t y = y0; y <= y1; ++y)
+        for (int64_t x = x0; x <= x1; ++x) {
+            float ndx = ((float)(2 * x + 1) / (float)W) - 1.0f;
+            float ndy = ((float)(2 * y + 1) / (float)H) - 1.0f;
+            float r[3] = {ndx / fx, ndy / fy, -1.0f};
+            float pv[3];
+            cross3(r, e2, pv);
+            float det = dot3(e1, pv);
+            if (!(det > 0.0f)) continue;
+            float u = dot3(tv, pv) / det;
+            float w = dot3(r, qv) / det;
+            float b0 = 1.0f - u;
+            b0 = b0 - w;
+            float t = dot3(e2, qv) / det;
+            if (!(u >= 0.0f && w >= 0.0f && b0 >= 0.0f && t >= nearv)) continue;
+            uint32_t bits;
+            memcpy(&bits, &t, 4);
+            uint64_t key = ((uint64_t)(bits >> 3) << 36) | (id & ORC_ID_MASK);
+            size_t pix = (size_t)y * (size_t)W + (size_t)x;
+            if (key < vis[pix]) vis[pix] = key;
+        }
+    (void)H;
+}
+
+/* The visibility buffer with the paper's ray-cast stage 3 (reading R16).
+ * Which triangles reach it follows the stage thresholds of Sections 4.1 and
+ * 4.2, s1_max and s2_max pixel centres:
+ *   - a vertex outside the near plane or the guard band sends the triangle
+ *     on to stage 2, unless all three lie outside one plane (dropped);
+ *   - otherwise the snapped triangle decides: area <= 0 is dropped (back
+ *     face), a bbox without a pixel centre on screen is dropped, an extent of
+ *     2^14 subpixels or more, or more than s1_max pixel centres, goes on to
+ *     stage 2, and every other triangle is rasterized with edge functions;
+ *   - in stage 2 the clipped polygon's snapped bbox, clamped to the screen,
+ *     decides: more than s2_max pixel centres take the ray cast over exactly
+ *     those pixels, fewer take edge functions like everything else.
+ * vis (W x H, row 0 = bottom) must start all ones. */
+int orc_render_paper(const orc_mesh *meshes, int n_meshes, const orc_instance *inst, int n_inst,
+                     const orc_camera *cam, uint32_t s1_max, uint32_t s2_max, uint64_t *vis)
+{
+    float cp[3];
+    if (orc_camera_params(cam->proj, cp) != ORC_OK) return ORC_BAD_CAMERA;
+    if (cam->W <= 0 || cam->H <= 0 || cam->W > ORC_MAX_WH || cam->H > ORC_MAX_WH) return ORC_BAD_ARG;
+    if (!is_affine(cam->view)) return ORC_NOT_AFFINE;
+    uint64_t *base = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)n_inst + 1));
+    int st = orc_bases(meshes, n_meshes, inst, n_inst, base);
+    if (st != ORC_OK) { free(base); return st; }
+    float fx = cp[0], fy = cp[1], nearv = cp[2];
+    int W = cam->W, H = cam->H;
+    float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
+    for (int i = 0; i < n_inst; ++i) {
+        const orc_mesh *m = &meshes[inst[i].mesh];
+        if (!is_affine(inst[i].model)) { free(base); return ORC_NOT_AFFINE; }
+        float mv[12];
+        orc_model_view(cam->view, inst[i].model, mv);
+        for (uint64_t t = 0; t < m->T; ++t) {
+            uint64_t id = base[i] + t;
+            float v[3][3], tri[9];
+            orc_cv c[3];
+            unsigned o[3];
+            for (int k = 0; k < 3; ++k) {
+                uint32_t vi = m->idx[3 * t + (uint64_t)k];
+                if ((uint64_t)vi >= m->V) { free(base); return ORC_BAD_INDEX; }
+                view_space(mv, m->pos + 3 * (uint64_t)vi, v[k]);
+                c[k] = to_clip(v[k], fx, fy);
+                tri[3 * k] = c[k].x; tri[3 * k + 1] = c[k].y; tri[3 * k + 2] = c[k].w;
+                o[k] = outcode5(c[k], nearv);
+            }
+            if (o[0] & o[1] & o[2]) continue;
+            if (!(o[0] | o[1] | o[2])) {
+                int32_t X[3], Y[3];
+                float iz[3];
+                for (int k = 0; k < 3; ++k) snap_vertex(c[k], hw, hh, &X[k], &Y[k], &iz[k]);
+                int64_t A = ((int64_t)X[1] - X[0]) * ((int64_t)Y[2] - Y[0]) -
+                            ((int64_t)X[2] - X[0]) * ((int64_t)Y[1] - Y[0]);
+                if (A <= 0) continue;
+                int64_t mnx = X[0], mxx = X[0], mny = Y[0], mxy = Y[0];
+                for (int k = 1; k < 3; ++k) {
+                    if (X[k] < mnx) mnx = X[k];
+                    if (X[k] > mxx) mxx = X[k];
+                    if (Y[k] < mny) mny = Y[k];
+                    if (Y[k] > mxy) mxy = Y[k];
+                }
+                int64_t x0, x1, y0, y1;
+                centre_range(mnx, mxx, W, &x0, &x1);
+                centre_range(mny, mxy, H, &y0, &y1);
+                if (x0 > x1 || y0 > y1) continue;
+                int large = mxx - mnx >= 16384 || mxy - mny >= 16384 ||
+                            (x1 - x0 + 1) * (y1 - y0 + 1) > (int64_t)s1_max;
+                if (!large) {
+                    raster_tri(X, Y, iz, id, W, H, 0, 1, vis);
+                    continue;
+                }
+            }
+            /* stage 2: the clipped polygon */
+            float poly[24];
+            int n = orc_clip(tri, nearv, poly);
+            if (n < 3) continue;
+            int32_t PX[8], PY[8];
+            float piz[8];
+            for (int k = 0; k < n; ++k) {
+                orc_cv q = {poly[3 * k], poly[3 * k + 1], poly[3 * k + 2]};
+                snap_vertex(q, hw, hh, &PX[k], &PY[k], &piz[k]);
+            }
+            int64_t mnx = PX[0], mxx = PX[0], mny = PY[0], mxy = PY[0];
+            for (int k = 1; k < n; ++k) {
+                if (PX[k] < mnx) mnx = PX[k];
+                if (PX[k] > mxx) mxx = PX[k];
+                if (PY[k] < mny) mny = PY[k];
+                if (PY[k] > mxy) mxy = PY[k];
+            }
+            int64_t x0, x1, y0, y1;
+            centre_range(mnx, mxx, W, &x0, &x1);
+            centre_range(mny, mxy, H, &y0, &y1);
+            if (x0 > x1 || y0 > y1) continue;
+            if ((x1 - x0 + 1) * (y1 - y0 + 1) > (int64_t)s2_max) {
+                raycast_range(v, fx, fy, nearv, W, H, x0, x1, y0, y1, id, vis);
+                continue;
+            }
+            for (int j = 1; j + 1 < n; ++j) {
+                int32_t sx[3] = {PX[0], PX[j], PX[j + 1]}, sy[3] = {PY[0], PY[j], PY[j + 1]};
+                float sz[3] = {piz[0], piz[j], piz[j + 1]};
+                raster_tri(sx, sy, sz, id, W, H, 0, 1, vis);
+            }
+        }
+    }
     free(base);
     return ORC_OK;
 }

@@ -63,6 +63,9 @@ def _lib():
             L.orc_render.restype = C.c_int
             L.orc_render.argtypes = [C.POINTER(_Mesh), C.c_int, C.POINTER(_Instance), C.c_int,
                                      C.POINTER(_Camera), C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+            L.orc_render_paper.restype = C.c_int
+            L.orc_render_paper.argtypes = [C.POINTER(_Mesh), C.c_int, C.POINTER(_Instance), C.c_int,
+                                           C.POINTER(_Camera), C.c_uint32, C.c_uint32, C.c_void_p]
             L.orc_resolve.argtypes = [C.POINTER(_Mesh), C.c_int, C.POINTER(_Instance), C.c_int,
                                       C.POINTER(_Camera), C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_interpolate.argtypes = [C.POINTER(_Mesh), C.c_int, C.POINTER(_Instance), C.c_int,
@@ -159,6 +162,18 @@ def render(osc: OracleScene, camera, first: int = 0, count=None, mode: int = 0,
                            first, count, mode, int(cull_back), out.ctypes.data)
     if st != 0:
         raise ValueError(f"orc_render failed: {st}")
+    return out
+
+
+def render_paper(osc: OracleScene, camera, s1_max: int = 128, s2_max: int = 4096) -> np.ndarray:
+    """Visibility buffer with the paper's ray-cast stage 3: triangles whose
+    visible bbox on reaching stage 2 holds more than s2_max pixel centres are
+    covered by view-space pixel rays, every other one by edge functions."""
+    out = np.full((camera.H, camera.W), EMPTY, np.uint64)
+    st = _lib().orc_render_paper(osc.meshes, osc.n_meshes, osc.inst, osc.n_inst, C.byref(_cam(camera)),
+                                 s1_max, s2_max, out.ctypes.data)
+    if st != 0:
+        raise ValueError(f"orc_render_paper failed: {st}")
     return out
 
 

@@ -27,7 +27,8 @@ C_MUTATIONS = [
      "int64_t px = 256 * x + 128, py = 256 * y;"),
     ("depth, wrong iz index", "float s2 = (float)E2 * iz[2];", "float s2 = (float)E2 * iz[1];"),
     ("depth, dropped term", "            s = s + s2;\n", "            s = s + 0.0f * s2;\n"),
-    ("word, 4 mantissa bits dropped", "((uint64_t)(bits >> 3) << 36)", "((uint64_t)(bits >> 4) << 36)"),
+    ("word, 4 mantissa bits dropped", "memcpy(&bits, &depth, 4);\n            uint64_t key = ((uint64_t)(bits >> 3) << 36)",
+     "memcpy(&bits, &depth, 4);\n            uint64_t key = ((uint64_t)(bits >> 4) << 36)"),
     ("transform, dropped translation", "        s = s + mv[4 * r + 3];\n", "        s = s + 0.0f;\n"),
     ("transform, dropped z term", "        s = s + c;\n        s = s + mv", "        s = s + 0.0f * c;\n        s = s + mv"),
     ("model-view, transposed product", "(double)view[4 * r + k] * (double)model[4 * k + c]",
@@ -43,7 +44,7 @@ C_MUTATIONS = [
     ("no backface cull", "        if (cull_back) return;\n", "        if (0) return;\n"),
     ("id bases off by one", "        base[i] = acc;\n", "        base[i] = acc + (i > 0);\n"),
     ("resolve, lower bound", "if (a[mid] <= key) lo = mid + 1;", "if (a[mid] < key) lo = mid + 1;"),
-    ("resolve, sign of w", "float w = dot3(r, qv) / det;", "float w = -dot3(r, qv) / det;"),
+    ("resolve, sign of w", "qv);\n    float w = dot3(r, qv) / det;", "qv);\n    float w = -dot3(r, qv) / det;"),
     ("resolve, ray fx and fy swapped", "float r[3] = {ndx / cp[0], ndy / cp[1], -1.0f};",
      "float r[3] = {ndx / cp[1], ndy / cp[0], -1.0f};"),
     ("resolve, pixel centre", "float ndx = ((float)(2 * x + 1) / (float)cam->W) - 1.0f;",
@@ -57,6 +58,11 @@ C_MUTATIONS = [
     ("quantization, 65536 levels", "v = rint(65535.0 * (", "v = rint(65536.0 * ("),
     ("dequantization, lo dropped", "pos[3 * i + a] = fmaf((float)q[3 * i + a], step[a], lo[a]);",
      "pos[3 * i + a] = fmaf((float)q[3 * i + a], step[a], 0.0f);"),
+    ("ray cast, facing sign", "if (!(det > 0.0f)) continue;", "if (!(det < 0.0f)) continue;"),
+    ("ray cast, near test dropped", "t >= nearv)) continue;", "t >= 0.0f)) continue;"),
+    ("ray cast, b0 from u twice", "            b0 = b0 - w;\n            float t", "            b0 = b0 - u;\n            float t"),
+    ("ray cast, depth from e1", "float t = dot3(e2, qv) / det;", "float t = dot3(e1, qv) / det;"),
+    ("ray cast routing, s2 threshold", "> (int64_t)s2_max) {", ">= (int64_t)s2_max) {"),
 ]
 
 PY_MUTATIONS = [

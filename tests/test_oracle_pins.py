@@ -673,3 +673,119 @@ def test_adjoint_matches_central_differences(oracle_lib):
             cm_[v, ax] -= h
             fd = (L(pos, cp_) - L(pos, cm_)) / (2 * h)
             assert fd == pytest.approx(dcol[v, ax], rel=1e-6, abs=1e-9)
+
+
+# ------------------------------------------- paper-mode stage 3 (R16) ---
+def _ray_hits64(fx, fy, tri_view, W, H):
+    """float64 barycentrics (b0, b1, b2) and hit distance t of every
+    pixel-centre ray (ndx / fx, ndy / fy, -1) with a view-space triangle,
+    from a direct 3x3 solve of v0 + b1 e1 + b2 e2 = t r."""
+    v = np.asarray(tri_view, np.float64)
+    x = (2 * np.arange(W) + 1) / W - 1
+    y = (2 * np.arange(H) + 1) / H - 1
+    r = np.stack(np.broadcast_arrays(x[None, :] / fx, y[:, None] / fy, -np.ones((H, W))), -1)
+    e1, e2 = v[1] - v[0], v[2] - v[0]
+    M = np.stack([np.broadcast_to(e1, (H, W, 3)), np.broadcast_to(e2, (H, W, 3)), -r], -1)
+    sol = np.linalg.solve(M, np.broadcast_to(-v[0], (H, W, 3))[..., None])[..., 0]
+    b1, b2, t = sol[..., 0], sol[..., 1], sol[..., 2]
+    return 1 - b1 - b2, b1, b2, t
+
+
+def test_paper_stage3_plane_depth_closed_form(oracle_lib):
+    """The paper's ray-cast stage 3 on a quad at view depth D that fills the
+    frustum (far beyond stage 1's and stage 2's limits): every depth within
+    one 28-bit step of bits(D) >> 3, each triangle covering the pixels on its
+    side of the diagonal.  The ray cast is not watertight: a pixel centre
+    within rounding of the shared diagonal may be missed by both triangles,
+    and only there may a pixel stay empty."""
+    O = oracle_lib
+    W, H = 64, 48
+    for D in (0.37, 3.0, 250.0):
+        h = 4 * D
+        pos = [[-h, -h, -D], [h, -h, -D], [-h, h, -D], [h, h, -D]]
+        sc = Scene([mesh_np(pos, [[0, 1, 2], [1, 3, 2]])], [Instance(0, ident())])
+        proj = S.perspective(60, W / H, 0.01, 1000.0)
+        cam = _cam(np.eye(4), proj, W, H)
+        fx, fy, _ = O.camera_params(proj)
+        vis = O.render_paper(O.OracleScene(sc), cam, s1_max=128, s2_max=1000)
+        d28, ids = O.decode(vis)
+        hit = vis != O.EMPTY
+        assert hit.sum() >= W * H - max(W, H)
+        assert np.abs(d28.astype(np.int64) - (f32bits(D) >> 3))[hit].max() <= 1
+        # the diagonal from (h, -h) to (-h, h): side of each pixel's float64 hit
+        t0 = _ray_hits64(fx, fy, np.asarray(pos)[[0, 1, 2]], W, H)
+        t1 = _ray_hits64(fx, fy, np.asarray(pos)[[1, 3, 2]], W, H)
+        m0 = np.minimum(np.minimum(t0[0], t0[1]), t0[2])
+        m1 = np.minimum(np.minimum(t1[0], t1[1]), t1[2])
+        assert (ids[hit & (m0 > 1e-5)] == 0).all() and (ids[hit & (m1 > 1e-5)] == 1).all()
+        assert (np.maximum(m0, m1)[~hit] < 1e-5).all()
+
+
+def _tri_scene(tri_view):
+    return Scene([mesh_np(tri_view, [[0, 1, 2]])], [Instance(0, ident())])
+
+
+@pytest.mark.parametrize("case", ["inside", "near-crossing"])
+def test_paper_stage3_coverage_and_depth_match_float64_rays(oracle_lib, case):
+    """A large front-facing triangle (inside the frustum, or crossing the
+    near plane): pixels whose float64 ray hits clearly inside it and in front
+    of the near plane are covered at depth t (relative 1e-5, 3e-5 at grazing
+    incidence), pixels clearly outside are not; the same triangle wound the
+    other way covers nothing."""
+    O = oracle_lib
+    W, H = 96, 64
+    near = 0.05
+    proj = S.perspective(70, W / H, near, 100.0)
+    fx, fy, nv = O.camera_params(proj)
+    if case == "inside":
+        tri = [[-2.0, -1.5, -4.0], [2.5, -1.0, -6.0], [-0.5, 2.0, -3.0]]
+    else:
+        # a tilted ground plane just below the camera, two vertices behind
+        # it: the near plane cuts it along a slanted screen line, so the
+        # clipped polygon's bbox also holds pixels that see the plane closer
+        # than the near plane
+        tri = [[-3.0, -1.21, 1.0], [3.0, 1.19, 1.0], [0.0, -0.01, -8.0]]
+    cam = _cam(np.eye(4), proj, W, H)
+    b0, b1, b2, t = _ray_hits64(fx, fy, tri, W, H)
+    vis = O.render_paper(O.OracleScene(_tri_scene(tri)), cam, s1_max=128, s2_max=256)
+    bmin = np.minimum(np.minimum(b0, b1), b2)
+    inside = (bmin > 1e-5) & (t > nv * (1 + 1e-5))
+    outside = (bmin < -1e-5) | (t < nv * (1 - 1e-5))
+    assert inside.sum() > 300
+    if case == "near-crossing":
+        assert ((bmin > 1e-5) & (t > 0) & (t < nv * (1 - 1e-5))).sum() > 100
+    assert (vis[inside] != O.EMPTY).all()
+    assert (vis[outside] == O.EMPTY).all()
+    d = O.decode(vis)[0][inside].astype(np.int64)
+    tb = np.array([f32bits(x) >> 3 for x in t[inside]], np.int64)
+    # one 28-bit step is 2^-20 relative; the FP32 ray cast loses a few more
+    # bits at grazing angles (the tilted ground): 32 steps is 3e-5 relative
+    assert np.abs(d - tb).max() <= (11 if case == "inside" else 32)
+    back = [tri[0], tri[2], tri[1]]
+    vb = O.render_paper(O.OracleScene(_tri_scene(back)), cam, s1_max=128, s2_max=256)
+    assert (vb == O.EMPTY).all()
+
+
+def test_paper_stage3_routing_thresholds(oracle_lib):
+    """Only triangles past stage 1 (more than s1_max centres) whose visible
+    bbox holds more than s2_max pixel centres are ray cast: with s2_max at
+    the bbox's count the result is the edge-function one bit for bit, one
+    below it the depths come from the ray cast; a triangle within s1_max is
+    never ray cast."""
+    O = oracle_lib
+    W, H = 80, 60
+    proj = S.perspective(60, W / H, 0.05, 100.0)
+    cam = _cam(np.eye(4), proj, W, H)
+    fx, fy, nv = O.camera_params(proj)
+    tri = np.array([[-1.1, -0.9, -3.0], [1.3, -0.6, -5.0], [-0.2, 1.2, -2.5]], np.float32)
+    osc = O.OracleScene(_tri_scene(tri))
+    _, XY, _, _ = O.project(np.eye(4, dtype=np.float32)[:3], np.array([fx, fy, nv], np.float32), W, H, tri)
+    lo = np.maximum(-((128 - XY.min(0).astype(np.int64)) // 256), 0)
+    hi = np.minimum((XY.max(0).astype(np.int64) - 128) // 256, [W - 1, H - 1])
+    K = int((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1))
+    assert K > 128
+    edge = O.render(osc, cam)
+    np.testing.assert_array_equal(O.render_paper(osc, cam, s1_max=128, s2_max=K), edge)
+    ray = O.render_paper(osc, cam, s1_max=128, s2_max=K - 1)
+    assert (O.decode(ray)[0] != O.decode(edge)[0]).any()
+    np.testing.assert_array_equal(O.render_paper(osc, cam, s1_max=K, s2_max=32), edge)
