@@ -74,8 +74,10 @@ typedef struct {
     uint64_t *vis;
 } curast_view;
 
-/* Tunables.  None of them changes a visibility buffer: every triangle is
- * covered by the same exact rule whichever stage rasterizes it. */
+/* Tunables.  None of them but stage3_raycast changes a visibility buffer:
+ * every triangle is covered by the same exact rule whichever stage
+ * rasterizes it.  With stage3_raycast on, stage1_max_pixels and
+ * stage2_max_pixels also decide which triangles are ray cast. */
 typedef struct {
     uint32_t stage1_max_pixels;  /* stage 1 rasterizes bbox <= this (paper: 128), 1..1024   */
     uint32_t stage2_max_pixels;  /* stage 2 rasterizes bbox <= this (paper: 4096), >= 32     */
@@ -93,7 +95,12 @@ typedef struct {
                                     pairs test each step's 64 triangles as one box per pair
                                     before the per-triangle cull (default 2); 0 turns the
                                     group test off, 0..64                                    */
-    uint32_t reserved;           /* 0                                                        */
+    uint32_t stage3_raycast;     /* 1: the paper's stage 3 (Section 4.3): a triangle whose
+                                    visible bbox, on reaching stage 2, holds more than
+                                    stage2_max_pixels pixel centres is covered by view-space
+                                    pixel-centre rays instead of the fixed-point rule (the
+                                    result then follows the ray-cast reading, not the
+                                    default one); 0 (default): one fixed-point rule for all */
 } curast_config;
 
 /* Counters read back by curast_sync.  Stats fields are filled only when

@@ -107,11 +107,13 @@ struct Q1Entry {             // stage 1 -> stage 2: a whole triangle of one pair
 };
 
 struct Q2Entry {             // stage 2 -> stage 3: one tile of one sub-triangle
-    int32_t X[3], Y[3];
+    int32_t X[3], Y[3];      // ray entries: X = (x0, x1, 0), Y = (y0, y1, 0), the pixel range
     float iz[3];
     uint32_t view;
     uint64_t id;
     uint32_t tx, ty;         // tile coordinates
+    uint32_t pair;           // ray entries: the (instance, view) pair
+    uint32_t ray;            // 1: the paper's ray-cast stage 3 over the whole triangle
 };
 
 struct Counters {
@@ -155,6 +157,7 @@ struct FrameDev {
     uint32_t check;          // bounds-check indices
     uint32_t stats;          // count statistics
     uint32_t group_min;      // instanced items with >= this many pairs (> 0) run the group test
+    uint32_t s3_ray;         // 1: triangles past s2_max take the paper's ray-cast stage 3
 };
 
 constexpr unsigned kErrIndex = 1u;     // a vertex index >= V was skipped
@@ -346,6 +349,89 @@ __device__ __forceinline__ void raster_range(const SubTri &s, int x0, int x1, in
         const int y = y0 + (int)(i / w);
         const int x = x0 + (int)(i - (int64_t)(y - y0) * w);
         shade_pixel(s, x, y, vis, W);
+    }
+}
+
+// ---------------------------------------------------- view-space rays --
+// view-space vertex: row r of MV as ((m0 x + m1 y) + m2 z) + m3 (Section 4.1)
+__device__ __forceinline__ float3 view_space(const float *m, const float *p) {
+    float3 v;
+    v.x = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[0], p[0]), __fmul_rn(m[1], p[1])), __fmul_rn(m[2], p[2])), m[3]);
+    v.y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[4], p[0]), __fmul_rn(m[5], p[1])), __fmul_rn(m[6], p[2])), m[7]);
+    v.z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[8], p[0]), __fmul_rn(m[9], p[1])), __fmul_rn(m[10], p[2])), m[11]);
+    return v;
+}
+
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) {
+    return make_float3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)),
+                       __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+                       __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)), __fmul_rn(a.z, b.z));
+}
+
+// Pixel-centre ray through (x, y): (ndx / fx, ndy / fy, -1) with
+// ndx = (2x + 1) / W - 1 (camera at the origin of view space).
+__device__ __forceinline__ float3 pixel_ray(int x, int y, int W, int H, float fx, float fy) {
+    const float ndx = __fsub_rn(__fdiv_rn(__int2float_rn(2 * x + 1), __int2float_rn(W)), 1.0f);
+    const float ndy = __fsub_rn(__fdiv_rn(__int2float_rn(2 * y + 1), __int2float_rn(H)), 1.0f);
+    return make_float3(__fdiv_rn(ndx, fx), __fdiv_rn(ndy, fy), -1.0f);
+}
+
+// Pixel centres 256 i + 128 inside the snapped range [mn, mx] (1/256 px) of
+// an n-pixel axis (arithmetic shifts are floor divisions), clamped to the
+// screen; lo > hi when there are none.
+__device__ __forceinline__ void centre_range(int mn, int mx, int n, int &lo, int &hi) {
+    lo = max(-((128 - mn) >> 8), 0);
+    hi = min((mx - 128) >> 8, n - 1);
+}
+
+// The paper's stage 3 (Section 4.3): a ray from the camera through each
+// pixel centre, intersected with the triangle in view space.  With
+// e1 = v1 - v0, e2 = v2 - v0, p = r x e2, det = e1.p, u = (-v0).p / det,
+// q = (-v0) x e1, w = r.q / det, b0 = (1 - u) - w and t = e2.q / det, the
+// pixel is covered when det > 0 (the front side faces the camera), u, w and
+// b0 are >= 0 and t >= near, at depth t (the view-space distance along -z).
+struct RayTri { float3 e1, e2, tv, qv; };
+
+__device__ __forceinline__ RayTri ray_setup(float3 v0, float3 v1, float3 v2) {
+    RayTri R;
+    R.e1 = sub3(v1, v0);
+    R.e2 = sub3(v2, v0);
+    R.tv = make_float3(-v0.x, -v0.y, -v0.z);
+    R.qv = cross3(R.tv, R.e1);
+    return R;
+}
+
+__device__ __forceinline__ void ray_pixel(const RayTri &R, int x, int y, const ViewDev &vw, uint64_t id) {
+    const float3 r = pixel_ray(x, y, vw.W, vw.H, vw.fx, vw.fy);
+    const float3 pv = cross3(r, R.e2);
+    const float det = dot3(R.e1, pv);
+    if (!(det > 0.0f)) return;
+    const float u = __fdiv_rn(dot3(R.tv, pv), det);
+    const float w = __fdiv_rn(dot3(r, R.qv), det);
+    const float b0 = __fsub_rn(__fsub_rn(1.0f, u), w);
+    const float t = __fdiv_rn(dot3(R.e2, R.qv), det);
+    if (!(u >= 0.0f && w >= 0.0f && b0 >= 0.0f && t >= vw.nearv)) return;
+    const uint64_t key = ((uint64_t)(__float_as_uint(t) >> 3) << 36) | (id & kIdMask);
+    depth_test_write(vw.vis, (size_t)y * (size_t)vw.W + (size_t)x, key);
+}
+
+// Pixels i = start, start + stride, ... of [x0, x1] x [y0, y1] by ray cast.
+__device__ __forceinline__ void ray_range(const RayTri &R, int x0, int x1, int y0, int y1, int start, int stride,
+                                          const ViewDev &vw, uint64_t id) {
+    const int w = x1 - x0 + 1;
+    const int64_t n = (int64_t)w * (int64_t)(y1 - y0 + 1);
+    for (int64_t i = start; i < n; i += stride) {
+        const int y = y0 + (int)(i / w);
+        const int x = x0 + (int)(i - (int64_t)(y - y0) * w);
+        ray_pixel(R, x, y, vw, id);
     }
 }
 

@@ -42,6 +42,39 @@ __device__ __noinline__ void raster_triangle_general(const CV c[3], const ViewDe
     }
 }
 
+// The triangle of global id `id` under pair `pidx` in view space, set up for
+// the ray cast of stage 3; false when an index is out of range.
+__device__ __forceinline__ bool ray_tri_of(const FrameDev &f, uint32_t pidx, uint64_t id, RayTri &R) {
+    const PairDev &pr = f.pairs[pidx];
+    const MeshDev &mesh = f.meshes[pr.mesh];
+    const uint64_t t = id - pr.base;
+    float3 v[3];
+    for (int k = 0; k < 3; ++k) {
+        const uint32_t vi = mesh_index(mesh, 3 * t + k);
+        if (vi >= mesh.V) return false;
+        float p[3];
+        mesh_vertex(mesh, vi, p[0], p[1], p[2]);
+        v[k] = view_space(pr.mv, p);
+    }
+    R = ray_setup(v[0], v[1], v[2]);
+    return true;
+}
+
+// Snapped bbox of a clipped polygon as a pixel-centre range on the screen;
+// returns the number of pixel centres (0 when there are none).
+__device__ __forceinline__ int64_t poly_range(const int *X, const int *Y, int n, int W, int H, int &x0, int &x1,
+                                              int &y0, int &y1) {
+    int mnx = X[0], mxx = X[0], mny = Y[0], mxy = Y[0];
+    for (int k = 1; k < n; ++k) {
+        mnx = min(mnx, X[k]); mxx = max(mxx, X[k]);
+        mny = min(mny, Y[k]); mxy = max(mxy, Y[k]);
+    }
+    centre_range(mnx, mxx, W, x0, x1);
+    centre_range(mny, mxy, H, y0, y1);
+    if (x0 > x1 || y0 > y1) return 0;
+    return (int64_t)(x1 - x0 + 1) * (int64_t)(y1 - y0 + 1);
+}
+
 __device__ __forceinline__ void stat_add(const FrameDev &f, int k, unsigned long long v) {
     if (f.stats && v) atomicAdd(&f.ctr->stats[k], v);
 }
@@ -68,6 +101,22 @@ __device__ __noinline__ void q1_overflow(const FrameDev *fp, uint64_t id, uint32
     const ViewDev &vw = f.views[f.pairs[pidx].view];
     CV c[3];
     load_clip(f, *mesh, pidx, t, vw, c);
+    if (f.s3_ray) {
+        // the stage-2 decision of the ray-cast mode: a visible bbox over
+        // s2_max pixel centres takes the ray cast, here by this thread alone
+        CV poly[kMaxPoly];
+        const int n = clip_polygon(c, vw.nearv, poly);
+        if (n < 3) return;
+        int X[kMaxPoly], Y[kMaxPoly];
+        float iz[kMaxPoly];
+        for (int k = 0; k < n; ++k) snap(poly[k], vw.hw, vw.hh, X[k], Y[k], iz[k]);
+        int x0, x1, y0, y1;
+        if (poly_range(X, Y, n, vw.W, vw.H, x0, x1, y0, y1) > (int64_t)f.s2_max) {
+            RayTri R;
+            if (ray_tri_of(f, pidx, id, R)) ray_range(R, x0, x1, y0, y1, 0, 1, vw, id);
+            return;
+        }
+    }
     raster_triangle_general(c, vw, id, 0, 1);
 }
 
@@ -211,12 +260,50 @@ __device__ __forceinline__ void q2_append(const FrameDev &f, bool want, const Su
         e.id = s.id;
         e.tx = (uint32_t)tx;
         e.ty = (uint32_t)ty;
+        e.pair = 0;
+        e.ray = 0;
         f.q2[slot] = e;
     } else {
         atomicAdd(&f.ctr->overflow2, 1ull);
         const int ts = 1 << f.tile_log2;
         raster_range(s, max(s.x0, tx * ts), min(s.x1, tx * ts + ts - 1), max(s.y0, ty * ts),
                      min(s.y1, ty * ts + ts - 1), 0, 1, vw.vis, vw.W);
+    }
+}
+
+// The same for one tile of a triangle that takes the ray-cast stage 3: the
+// entry names the triangle (id, pair) and its visible pixel range.
+__device__ __forceinline__ void q2_append_ray(const FrameDev &f, bool want, uint64_t id, uint32_t pidx, uint32_t view,
+                                              int x0, int x1, int y0, int y1, int tx, int ty, const ViewDev &vw) {
+    const unsigned active = __activemask();
+    const unsigned m = __ballot_sync(active, want);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&f.ctr->q2_count, (unsigned long long)__popc(m));
+    base = __shfl_sync(active, base, leader);
+    if (!want) return;
+    const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+    if (slot < f.q2_cap) {
+        Q2Entry e;
+        e.X[0] = x0; e.X[1] = x1; e.X[2] = 0;
+        e.Y[0] = y0; e.Y[1] = y1; e.Y[2] = 0;
+        e.iz[0] = e.iz[1] = e.iz[2] = 0.0f;
+        e.view = view;
+        e.id = id;
+        e.tx = (uint32_t)tx;
+        e.ty = (uint32_t)ty;
+        e.pair = pidx;
+        e.ray = 1;
+        f.q2[slot] = e;
+    } else {
+        atomicAdd(&f.ctr->overflow2, 1ull);
+        const int ts = 1 << f.tile_log2;
+        RayTri R;
+        if (ray_tri_of(f, pidx, id, R))
+            ray_range(R, max(x0, tx * ts), min(x1, tx * ts + ts - 1), max(y0, ty * ts), min(y1, ty * ts + ts - 1), 0,
+                      1, vw, id);
     }
 }
 
@@ -242,6 +329,27 @@ __global__ void __launch_bounds__(256) k_stage2(FrameDev f) {
         int X[kMaxPoly], Y[kMaxPoly];
         float iz[kMaxPoly];
         for (int k = 0; k < np; ++k) snap(poly[k], vw.hw, vw.hh, X[k], Y[k], iz[k]);
+        if (f.s3_ray) {
+            // the paper's stage 3: a triangle whose visible bbox holds more
+            // than s2_max pixel centres is ray cast over that range, in tiles
+            int x0, x1, y0, y1;
+            const int64_t cnt = poly_range(X, Y, np, vw.W, vw.H, x0, x1, y0, y1);
+            if (cnt == 0) continue;
+            if (cnt > (int64_t)f.s2_max) {
+                const int tl = (int)f.tile_log2;
+                const int tx0 = x0 >> tl, tx1 = x1 >> tl, ty0 = y0 >> tl, ty1 = y1 >> tl;
+                const int ntx = tx1 - tx0 + 1;
+                const int nt = ntx * (ty1 - ty0 + 1);
+                for (int kb = 0; kb < nt; kb += 32) {
+                    const int k = kb + lane;
+                    const bool want = k < nt;
+                    const int tx = tx0 + (want ? k % ntx : 0), ty = ty0 + (want ? k / ntx : 0);
+                    q2_append_ray(f, want, e.id, e.pair, pr.view, x0, x1, y0, y1, tx, ty, vw);
+                    n_parts += want;
+                }
+                continue;
+            }
+        }
         for (int j = 1; j + 1 < np; ++j) {
             SubTri s;
             s.X[0] = X[0]; s.X[1] = X[j]; s.X[2] = X[j + 1];
@@ -276,7 +384,9 @@ __global__ void __launch_bounds__(256) k_stage2(FrameDev f) {
 
 // ---------------------------------------------------------------- stage 3 --
 // Section 4.3: one block per tile part; its threads walk the tile's pixels
-// (restricted to the sub-triangle's bbox) line by line.
+// (restricted to the sub-triangle's bbox) line by line -- with edge
+// functions, or, in the ray-cast mode, with the paper's view-space pixel
+// rays against the whole (unclipped) triangle.
 __global__ void __launch_bounds__(256) k_stage3(FrameDev f) {
     __shared__ unsigned long long s_i;
     const unsigned long long total = *((volatile unsigned long long *)&f.ctr->q2_count);
@@ -290,6 +400,15 @@ __global__ void __launch_bounds__(256) k_stage3(FrameDev f) {
         if (i >= n) break;
         const Q2Entry e = f.q2[i];
         const ViewDev vw = f.views[e.view];
+        if (e.ray) {
+            RayTri R;
+            if (!ray_tri_of(f, e.pair, e.id, R)) continue;
+            const int x0 = max(e.X[0], (int)e.tx * ts), x1 = min(e.X[1], (int)e.tx * ts + ts - 1);
+            const int y0 = max(e.Y[0], (int)e.ty * ts), y1 = min(e.Y[1], (int)e.ty * ts + ts - 1);
+            if (x0 > x1 || y0 > y1) continue;
+            ray_range(R, x0, x1, y0, y1, threadIdx.x, blockDim.x, vw, e.id);
+            continue;
+        }
         SubTri s;
         for (int k = 0; k < 3; ++k) { s.X[k] = e.X[k]; s.Y[k] = e.Y[k]; s.iz[k] = e.iz[k]; }
         s.id = e.id;

@@ -549,6 +549,7 @@ FrameDev make_frame_dev(const curast_ctx *c) {
     f.tile_log2 = c->cfg.tile_log2;
     f.tpt = c->cfg.stage1_tri_per_thread;
     f.group_min = c->cfg.stage1_group_min_pairs;
+    f.s3_ray = c->cfg.stage3_raycast;
     f.check = c->cfg.check_indices;
     f.stats = c->cfg.collect_stats;
     return f;
@@ -761,7 +762,7 @@ bool valid_config(const curast_config &c) {
            c.pairs_per_segment >= 1 && c.pairs_per_segment <= 64 && c.queue1_capacity >= 1 &&
            c.queue2_capacity >= 1 && c.queue1_capacity <= (1ull << 32) && c.queue2_capacity <= (1ull << 32) &&
            c.stage1_bitmap_bytes >= (1ull << 12) && c.stage1_bitmap_bytes <= (1ull << 36) &&
-           c.stage1_group_min_pairs <= 64 && c.reserved == 0;
+           c.stage1_group_min_pairs <= 64 && c.stage3_raycast <= 1;
 }
 
 }  // namespace

@@ -4,29 +4,6 @@
 
 namespace curast {
 
-// view-space vertex: row r of MV as ((m0 x + m1 y) + m2 z) + m3 (Section 4.1)
-__device__ __forceinline__ float3 view_space(const float *m, const float *p) {
-    float3 v;
-    v.x = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[0], p[0]), __fmul_rn(m[1], p[1])), __fmul_rn(m[2], p[2])), m[3]);
-    v.y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[4], p[0]), __fmul_rn(m[5], p[1])), __fmul_rn(m[6], p[2])), m[7]);
-    v.z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[8], p[0]), __fmul_rn(m[9], p[1])), __fmul_rn(m[10], p[2])), m[11]);
-    return v;
-}
-
-__device__ __forceinline__ float3 sub3(float3 a, float3 b) {
-    return make_float3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
-}
-
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-    return make_float3(__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)),
-                       __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
-                       __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
-}
-
-__device__ __forceinline__ float dot3(float3 a, float3 b) {
-    return __fadd_rn(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)), __fmul_rn(a.z, b.z));
-}
-
 __device__ __forceinline__ float interp3(float b0, float b1, float b2, float c0, float c1, float c2) {
     return __fadd_rn(__fadd_rn(__fmul_rn(b0, c0), __fmul_rn(b1, c1)), __fmul_rn(b2, c2));
 }
@@ -40,14 +17,6 @@ __device__ __forceinline__ int find_instance(const uint64_t *base, int n, uint64
         if (base[mid] <= id) lo = mid + 1; else hi = mid;
     }
     return lo - 1;
-}
-
-// Pixel-centre ray through (x, y): (ndx / fx, ndy / fy, -1) with
-// ndx = (2x + 1) / W - 1 (camera at the origin of view space).
-__device__ __forceinline__ float3 pixel_ray(int x, int y, int W, int H, float fx, float fy) {
-    const float ndx = __fsub_rn(__fdiv_rn(__int2float_rn(2 * x + 1), __int2float_rn(W)), 1.0f);
-    const float ndy = __fsub_rn(__fdiv_rn(__int2float_rn(2 * y + 1), __int2float_rn(H)), 1.0f);
-    return make_float3(__fdiv_rn(ndx, fx), __fdiv_rn(ndy, fy), -1.0f);
 }
 
 // Barycentrics of the ray hit with the triangle's plane (Moeller-Trumbore

@@ -204,6 +204,7 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     f.tile_log2 = 6;
     f.tpt = 4;
     f.group_min = 0;
+    f.s3_ray = 0;
     f.check = 1;
     f.stats = 0;
 

@@ -1,0 +1,128 @@
+"""The paper's ray-cast stage 3 (Section 4.3) through the C ABI: with
+stage3_raycast on, triangles whose visible bbox holds more than
+stage2_max_pixels pixel centres are covered by view-space pixel rays, and the
+visibility buffers equal the oracle's orc_render_paper bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import oracle as orc
+from synthetic.scenes import Camera, Instance, Mesh, Scene
+
+from gpu_util import assert_vis_equal, upload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2604_21749_gb300 import api as A
+    return A
+
+
+def _renderer(api, **cfg):
+    r = api.Renderer(0)
+    r.set_config(stage3_raycast=1, **cfg)
+    return r
+
+
+def _paper(scene, cam, s1=128, s2=4096):
+    return orc.render_paper(orc.OracleScene(scene), cam, s1, s2)
+
+
+def _room():
+    """The camera inside a closed box (12 triangles facing inwards): every
+    face crosses the near plane or the guard band, so every one reaches
+    stage 2 and, being huge, the ray cast."""
+    p = np.array([[x, y, z] for x in (-3, 3) for y in (-2, 2) for z in (-4, 4)], np.float32)
+    quads = [(0, 1, 3, 2), (4, 6, 7, 5), (0, 4, 5, 1), (2, 3, 7, 6), (0, 2, 6, 4), (1, 5, 7, 3)]
+    idx = []
+    for a, b, c, d in quads:          # wound to face the inside
+        idx += [[a, c, b], [a, d, c]]
+    col = np.tile(np.array([[200, 120, 40, 255]], np.uint8), (8, 1))
+    m = Mesh(pos=torch.tensor(p), idx=torch.tensor(np.array(idx, np.int32)), rgba8=torch.tensor(col))
+    cams = [Camera(S.look_at((0.3, 0.1, 0.2), (1.0, -0.4, -2.0)), S.perspective(80, 1.5, 0.05, 100.0), 300, 200),
+            Camera(S.look_at((-2.5, 1.5, 3.5), (2.0, -1.0, -3.0)), S.perspective(100, 1.0, 0.01, 100.0), 160, 160)]
+    return Scene([m], [Instance(0, np.eye(4, dtype=np.float32))], cams)
+
+
+@pytest.mark.parametrize("cfg", [dict(), dict(stage2_max_pixels=32), dict(stage1_max_pixels=16, stage2_max_pixels=64),
+                                 dict(stage2_max_pixels=100000), dict(tile_log2=4)])
+def test_small_workload_ray_cast_equals_oracle(api, cfg):
+    """The heightfield plus two ground triangles crossing the near plane;
+    thresholds moved so that few, many or no triangles are ray cast."""
+    sc = S.scene_small()
+    cam = sc.cameras[0]
+    r = _renderer(api, **cfg)
+    keep = upload(r, sc)
+    vis = r.render(cam.view, cam.proj, cam.W, cam.H)
+    f32, u8 = r.resolve(cam.view, cam.proj, vis)
+    r.sync()
+    c = r.config
+    ref = _paper(sc, cam, c.stage1_max_pixels, c.stage2_max_pixels)
+    assert_vis_equal(vis, ref, f"ray-cast mode {cfg}")
+    osc = orc.OracleScene(sc)
+    rf, r8 = orc.resolve(osc, cam, ref)
+    np.testing.assert_allclose(f32.cpu().numpy(), rf, atol=1e-6, rtol=0)
+    np.testing.assert_array_equal(u8.cpu().numpy(), r8)
+    del keep
+
+
+def test_ray_cast_differs_from_the_fixed_point_rule(api):
+    """The mode is live: the ground triangles' depths come from the rays."""
+    sc = S.scene_small()
+    cam = sc.cameras[0]
+    r = _renderer(api)
+    keep = upload(r, sc)
+    vis = r.render(cam.view, cam.proj, cam.W, cam.H).cpu().numpy().view(np.uint64)
+    r.sync()
+    fixed = orc.render(orc.OracleScene(sc), cam)
+    assert (vis != fixed).sum() > 1000
+    del keep
+
+
+def test_room_around_the_camera(api):
+    sc = _room()
+    for cfg in (dict(), dict(queue1_capacity=1, queue2_capacity=1)):
+        r = _renderer(api, **cfg)
+        keep = upload(r, sc)
+        for cam in sc.cameras:
+            vis = r.render(cam.view, cam.proj, cam.W, cam.H)
+            r.sync()
+            ref = _paper(sc, cam)
+            assert (ref != orc.EMPTY).sum() > 0.9 * cam.W * cam.H
+            assert_vis_equal(vis, ref, f"room {cam.W}x{cam.H} {cfg}")
+        del keep
+
+
+def test_close_up_poses_ray_cast(api):
+    """Close-up poses of a 300^2 heightfield, triangles of hundreds of
+    pixels: with stage2_max_pixels = 32 most of them are ray cast."""
+    hf = S.heightfield_mesh(300, seed=100)
+    sc = Scene([hf], [Instance(0, np.eye(4, dtype=np.float32))], [])
+    r = _renderer(api, stage2_max_pixels=32)
+    keep = upload(r, sc)
+    for k in (0, 3, 5):
+        cam = S.camera_unique_pose(k, 480, 270)
+        vis = r.render(cam.view, cam.proj, cam.W, cam.H)
+        r.sync()
+        assert_vis_equal(vis, _paper(sc, cam, 128, 32), f"pose {k}")
+    del keep
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_views_ray_cast(api, use_graph):
+    from test_gpu_parity import _mixed_scene
+    sc = _mixed_scene()
+    r = _renderer(api, pairs_per_segment=7, stage2_max_pixels=64)
+    keep = upload(r, sc)
+    views = [(c.view, c.proj, c.W, c.H, None) for c in sc.cameras]
+    for frame in range(2):
+        out = r.render_batch(views, use_graph=use_graph)
+        r.sync()
+        for c, v in zip(sc.cameras, out):
+            assert_vis_equal(v, _paper(sc, c, 128, 64), f"batched {c.W}x{c.H} frame {frame}")
+    del keep
