@@ -49,6 +49,8 @@ def parse_args():
                    help="skip the 2x2 / 4x4 super-sampled frames")
     p.add_argument("--no-compressed", dest="compressed", action="store_false",
                    help="skip the frame with compressed geometry")
+    p.add_argument("--no-raycast", dest="raycast", action="store_false",
+                   help="skip the stage-3 workloads timed with the fixed-point rule and with the ray cast")
     p.add_argument("--subset", type=int, default=0,
                    help="profiling aid: give geometry only to this many tiles next to the view centre "
                         "(same layout, camera and triangle density; the other tiles are empty)")
@@ -370,6 +372,8 @@ def run_ours(args, ranks: Ranks):
     del sc, vis
     torch.cuda.empty_cache()
 
+    if ranks.rank == 0 and ranks.world == 1 and args.raycast:
+        result["raycast_stage3"] = raycast_stage3(args, dev)
     if ranks.rank == 0 and ranks.world == 1 and args.batched != "off":
         result["batched_vs_plain"] = batched_vs_plain(args, dev)
     if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
@@ -450,6 +454,58 @@ def supersampling(r, cam, args, ms_1x1, stream):
         out[f"{ss}x{ss}_resolve_ms"] = round(e1.elapsed_time(e2), 3)
         del vis
         torch.cuda.empty_cache()
+    return out
+
+
+def raycast_stage3(args, dev):
+    """Stage-3 workloads rendered with the default fixed-point rule and with
+    the paper's ray-cast stage 3 (stage3_raycast): the camera inside a closed
+    box at the frame size (every face huge and crossing the near plane), and
+    a close-up pose of a 1448^2 heightfield with stage2_max_pixels = 32 so
+    that its large triangles are ray cast.  Frame ms and stage-3 ms of each."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    from paper_2604_21749_gb300 import api
+    cases = []
+    room = S.scene_room(device=dev, W=args.W, H=args.H)
+    cases.append((f"room: 12 triangles around the camera, {args.W}x{args.H}", room, room.cameras[0], {}))
+    hf = S.heightfield_mesh(1448, seed=100, device=dev)
+    close = S.Scene([hf], [S.Instance(0, np.eye(4, dtype=np.float32))], [])
+    cases.append((f"close-up pose 3 of a 1448^2 heightfield, {args.W}x{args.H}, stage2_max_pixels 32", close,
+                  S.camera_unique_pose(3, args.W, args.H), {"stage2_max_pixels": 32}))
+    stream = torch.cuda.current_stream()
+    out = []
+    for name, sc, cam, cfg in cases:
+        r = api.Renderer(dev.index)
+        for m in sc.meshes:
+            r.upload_mesh(m.pos, m.idx, m.rgba8)
+        for it in sc.instances:
+            r.add_instance(it.mesh, it.model)
+        vis = r.new_vis(cam.W, cam.H)
+        row = {"workload": name}
+        for mode in (0, 1):
+            r.set_config(stage3_raycast=mode, **cfg)
+            for _ in range(3):
+                r.render(cam.view, cam.proj, cam.W, cam.H, vis)
+            r.sync()
+            frames = 20
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(frames):
+                r.render(cam.view, cam.proj, cam.W, cam.H, vis)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r.render(cam.view, cam.proj, cam.W, cam.H, vis)
+            st = r.stage_times()
+            key = "ray_cast" if mode else "fixed_point"
+            row[key + "_ms"] = round(e0.elapsed_time(e1) / frames, 4)
+            row[key + "_stage_ms"] = {k: round(v, 4) for k, v in
+                                      zip(["clear", "stage1_cull", "stage1_exact", "stage2", "stage3"], st)}
+        r.close()
+        out.append(row)
+        del vis
+    torch.cuda.empty_cache()
     return out
 
 

@@ -10,5 +10,5 @@ from .scenes import (  # noqa: F401
     value_noise, heightfield_mesh, sphere_mesh, ground_mesh,
     look_at, perspective,
     scene_small, scene_unique, camera_unique_pose, scene_billion, camera_billion,
-    scene_batched, scene_differentiable, target_colour_noise,
+    scene_batched, scene_differentiable, target_colour_noise, scene_room,
 )

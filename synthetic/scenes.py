@@ -362,6 +362,24 @@ def scene_batched(device="cpu", n_meshes: int = 256, n_instances: int = 10000,
     return Scene(meshes, inst, cams)
 
 
+def scene_room(device="cpu", W: int = 300, H: int = 200) -> Scene:
+    """The camera inside a closed 6 x 4 x 8 box whose 12 triangles face
+    inwards: every face crosses the near plane or the guard band and covers a
+    large part of the screen (a stage-3 workload).  Two cameras: W x H at 80
+    degrees near the centre, and a square 100-degree view from a corner."""
+    p = np.array([[x, y, z] for x in (-3, 3) for y in (-2, 2) for z in (-4, 4)], np.float32)
+    quads = [(0, 1, 3, 2), (4, 6, 7, 5), (0, 4, 5, 1), (2, 3, 7, 6), (0, 2, 6, 4), (1, 5, 7, 3)]
+    idx = []
+    for a, b, c, d in quads:          # wound to face the inside
+        idx += [[a, c, b], [a, d, c]]
+    col = np.tile(np.array([[200, 120, 40, 255]], np.uint8), (8, 1))
+    m = Mesh(pos=torch.tensor(p, device=device), idx=torch.tensor(np.array(idx, np.int32), device=device),
+             rgba8=torch.tensor(col, device=device))
+    cams = [Camera(look_at((0.3, 0.1, 0.2), (1.0, -0.4, -2.0)), perspective(80, W / H, 0.05, 100.0), W, H),
+            Camera(look_at((-2.5, 1.5, 3.5), (2.0, -1.0, -3.0)), perspective(100, 1.0, 0.01, 100.0), H, H)]
+    return Scene([m], [Instance(0, np.eye(4, dtype=np.float32))], cams)
+
+
 def scene_differentiable(device="cpu", n: int = 1448, W: int = 1024, H: int = 1024,
                          seed: int = 500) -> tuple:
     """Heightfield of n x n cells, FP32 RGB per-vertex colours from height.

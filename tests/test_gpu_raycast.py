@@ -8,7 +8,7 @@ import torch
 
 import synthetic as S
 from oracle import oracle as orc
-from synthetic.scenes import Camera, Instance, Mesh, Scene
+from synthetic.scenes import Instance, Scene
 
 from gpu_util import assert_vis_equal, upload
 
@@ -31,22 +31,6 @@ def _renderer(api, **cfg):
 
 def _paper(scene, cam, s1=128, s2=4096):
     return orc.render_paper(orc.OracleScene(scene), cam, s1, s2)
-
-
-def _room():
-    """The camera inside a closed box (12 triangles facing inwards): every
-    face crosses the near plane or the guard band, so every one reaches
-    stage 2 and, being huge, the ray cast."""
-    p = np.array([[x, y, z] for x in (-3, 3) for y in (-2, 2) for z in (-4, 4)], np.float32)
-    quads = [(0, 1, 3, 2), (4, 6, 7, 5), (0, 4, 5, 1), (2, 3, 7, 6), (0, 2, 6, 4), (1, 5, 7, 3)]
-    idx = []
-    for a, b, c, d in quads:          # wound to face the inside
-        idx += [[a, c, b], [a, d, c]]
-    col = np.tile(np.array([[200, 120, 40, 255]], np.uint8), (8, 1))
-    m = Mesh(pos=torch.tensor(p), idx=torch.tensor(np.array(idx, np.int32)), rgba8=torch.tensor(col))
-    cams = [Camera(S.look_at((0.3, 0.1, 0.2), (1.0, -0.4, -2.0)), S.perspective(80, 1.5, 0.05, 100.0), 300, 200),
-            Camera(S.look_at((-2.5, 1.5, 3.5), (2.0, -1.0, -3.0)), S.perspective(100, 1.0, 0.01, 100.0), 160, 160)]
-    return Scene([m], [Instance(0, np.eye(4, dtype=np.float32))], cams)
 
 
 @pytest.mark.parametrize("cfg", [dict(), dict(stage2_max_pixels=32), dict(stage1_max_pixels=16, stage2_max_pixels=64),
@@ -85,7 +69,11 @@ def test_ray_cast_differs_from_the_fixed_point_rule(api):
 
 
 def test_room_around_the_camera(api):
-    sc = _room()
+    """The camera inside a closed box (12 triangles facing inwards): every
+    face crosses the near plane or the guard band, so every one reaches
+    stage 2 and, being huge, the ray cast; with queue capacities of 1 the
+    overflow paths ray cast in place."""
+    sc = S.scene_room()
     for cfg in (dict(), dict(queue1_capacity=1, queue2_capacity=1)):
         r = _renderer(api, **cfg)
         keep = upload(r, sc)
