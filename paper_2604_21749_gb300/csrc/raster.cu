@@ -101,9 +101,21 @@ __device__ __noinline__ void q1_overflow(const FrameDev *fp, uint64_t id, uint32
     const ViewDev &vw = f.views[f.pairs[pidx].view];
     CV c[3];
     load_clip(f, *mesh, pidx, t, vw, c);
-    if (f.s3_ray) {
-        // the stage-2 decision of the ray-cast mode: a visible bbox over
-        // s2_max pixel centres takes the ray cast, here by this thread alone
+    raster_triangle_general(c, vw, id, 0, 1);
+}
+
+// The same in the ray-cast mode, with its stage-2 decision: a visible bbox
+// over s2_max pixel centres takes the ray cast, here by this thread alone.
+// (A function of its own: the fixed-point kernels never reach it, and its
+// frame does not weigh on their register allocation.)
+__device__ __noinline__ void q1_overflow_ray(const FrameDev *fp, uint64_t id, uint32_t pidx, const MeshDev *mesh,
+                                             uint64_t t) {
+    const FrameDev &f = *fp;
+    atomicAdd(&f.ctr->overflow1, 1ull);
+    const ViewDev &vw = f.views[f.pairs[pidx].view];
+    CV c[3];
+    load_clip(f, *mesh, pidx, t, vw, c);
+    {
         CV poly[kMaxPoly];
         const int n = clip_polygon(c, vw.nearv, poly);
         if (n < 3) return;
@@ -123,6 +135,7 @@ __device__ __noinline__ void q1_overflow(const FrameDev *fp, uint64_t id, uint32
 // Warp-aggregated append to queue 1 (ballot + popc + one atomicAdd per warp).
 // Lanes whose slot lies beyond the capacity rasterize their triangle in place.
 // f must live in parameter or global memory (its address is passed on).
+template <bool RAY>
 __device__ __forceinline__ void q1_append(const FrameDev &f, bool want, uint64_t id, uint32_t pidx,
                                           const MeshDev *mesh, uint64_t t) {
     const unsigned active = __activemask();
@@ -142,7 +155,8 @@ __device__ __forceinline__ void q1_append(const FrameDev &f, bool want, uint64_t
         e.pad = 0;
         f.q1[slot] = e;
     } else {
-        q1_overflow(&f, id, pidx, mesh, t);
+        if (RAY) q1_overflow_ray(&f, id, pidx, mesh, t);
+        else q1_overflow(&f, id, pidx, mesh, t);
     }
 }
 
@@ -482,7 +496,8 @@ cudaError_t query_launch_shape(LaunchShape *o, int device) {
     if ((e = stage1_shape<true, false, false>(&o->stage1_blocks_per_sm[1][0])) != cudaSuccess) return e;
     if ((e = stage1_shape<true, true, false>(&o->stage1_blocks_per_sm[1][1])) != cudaSuccess) return e;
     if ((e = stage1_shape<true, false, true>(&o->stage1_blocks_per_sm[1][2])) != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1x_blocks_per_sm, k_stage1_exact, 32 * s1::kExactWarps, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1x_blocks_per_sm, k_stage1_exact<false>,
+                                                      32 * s1::kExactWarps, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage2_blocks_per_sm, k_stage2, 256, 0);
     if (e != cudaSuccess) return e;
@@ -515,7 +530,8 @@ cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32
 }
 
 cudaError_t launch_stage1_exact(const FrameDev &f, uint32_t r, int blocks, cudaStream_t s) {
-    k_stage1_exact<<<blocks, 32 * s1::kExactWarps, 0, s>>>(f, r);
+    if (f.s3_ray) k_stage1_exact<true><<<blocks, 32 * s1::kExactWarps, 0, s>>>(f, r);
+    else k_stage1_exact<false><<<blocks, 32 * s1::kExactWarps, 0, s>>>(f, r);
     return cudaGetLastError();
 }
 

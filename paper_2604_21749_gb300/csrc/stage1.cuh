@@ -253,6 +253,7 @@ __device__ __forceinline__ void exact_gather(const FrameDev &f, uint2 e, bool li
 }
 
 // The exact path given the triangle's positions (from exact_gather).
+template <bool RAY>
 __device__ __forceinline__ void exact_compute(const FrameDev &f, uint2 e, bool live, const Tri9 &p) {
     const uint32_t pidx = live ? e.y : 0u;
     const uint64_t t = live ? e.x : 0u;
@@ -274,7 +275,7 @@ __device__ __forceinline__ void exact_compute(const FrameDev &f, uint2 e, bool l
         cls = classify(f, r, vw, x0, x1, y0, y1, A, st);
     }
     const uint64_t id = pr.base + t;
-    q1_append(f, cls == kQueue, id, pidx, mesh, t);
+    q1_append<RAY>(f, cls == kQueue, id, pidx, mesh, t);
     if (cls == kSmall) {
         const int X[3] = {r[0].X, r[1].X, r[2].X}, Y[3] = {r[0].Y, r[1].Y, r[2].Y};
         const float iz[3] = {r[0].iz, r[1].iz, r[2].iz};
@@ -287,10 +288,12 @@ __device__ __forceinline__ void exact_compute(const FrameDev &f, uint2 e, bool l
     }
 }
 
+// (the fused kernel serves the no-allocation entry point, which has no
+// ray-cast mode)
 __device__ __forceinline__ void exact_body(const FrameDev &f, uint2 e, bool live) {
     Tri9 p;
     exact_gather(f, e, live, p);
-    exact_compute(f, e, live, p);
+    exact_compute<false>(f, e, live, p);
 }
 
 // Out-of-line copy for the fused cull kernel (no survivor bitmap), which
@@ -740,6 +743,7 @@ constexpr int kExactBlocks = 5;                      // 96 registers a thread
 constexpr int kExactK = 3;                           // survivors a lane gathers together
 constexpr int kBatch = 32 * kExactK;
 }
+template <bool RAY>
 __global__ void __launch_bounds__(32 * s1::kExactWarps, s1::kExactBlocks)
     k_stage1_exact(const __grid_constant__ FrameDev f, uint32_t r) {
     using namespace s1;
@@ -830,7 +834,7 @@ __global__ void __launch_bounds__(32 * s1::kExactWarps, s1::kExactBlocks)
             Tri9 q;
 #pragma unroll
             for (int c = 0; c < 9; ++c) q.v[c] = stage[warp][u][c][lane];
-            exact_compute(f, buf[warp][live[u] ? lane + 32 * u : 0], live[u], q);
+            exact_compute<RAY>(f, buf[warp][live[u] ? lane + 32 * u : 0], live[u], q);
         }
     }
 }
