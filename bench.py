@@ -534,6 +534,12 @@ def batched_vs_plain(args, dev):
     views = [(c.view, c.proj, c.W, c.H, r.new_vis(c.W, c.H)) for c in sc.cameras]
     plain_out = [r.new_vis(c.W, c.H) for c in sc.cameras]
     stream = torch.cuda.current_stream()
+    # the workload's configuration is autotuned (its result is kept only if
+    # the buffers stay identical); both paths then run with it
+    t0 = time.perf_counter()
+    tuned = r.autotune(views)
+    torch.cuda.synchronize()
+    ttune = time.perf_counter() - t0
 
     def batched():
         r.render_batch(views, use_graph=True)
@@ -573,7 +579,10 @@ def batched_vs_plain(args, dev):
            "batched_gtris_s": round(info["triangles"] / (tb * 1e-3) / 1e9, 2),
            "batched_stage_ms": {k: round(v, 3) for k, v in
                                 zip(["clear", "stage1_cull", "stage1_exact", "stage2", "stage3"], st)},
-           "batched_stats": {k: v for k, v in stats.items() if v}, "generation_s": round(tgen, 1)}
+           "batched_stats": {k: v for k, v in stats.items() if v}, "generation_s": round(tgen, 1),
+           "autotuned": {k: tuned[k] for k in ("stage1_tri_per_thread", "stage1_max_pixels", "stage2_max_pixels",
+                                               "tile_log2", "pairs_per_segment", "stage1_group_min_pairs")},
+           "autotune_s": round(ttune, 1)}
     r.close()
     del sc, views, plain_out
     torch.cuda.empty_cache()

@@ -298,8 +298,9 @@ curast_status curast_sync(curast_ctx *ctx, curast_stream stream, curast_stats *s
  * [4] stage 3; waits for them. */
 curast_status curast_stage_times(curast_ctx *ctx, float out[5]);
 
-/* Picks stage thresholds, tile size and batch shape for the given views by
- * timing candidate configurations with curast_render_batch.  A candidate is
+/* Picks stage thresholds, tile size, batch shape, pairs per work item and the
+ * group-test threshold for the given views by timing candidate
+ * configurations with curast_render_batch (coordinate descent).  A candidate is
  * kept only if its visibility buffers equal the default configuration's bit
  * for bit.  The winner is installed and returned in *chosen (may be NULL).
  * The views' buffers are overwritten. */

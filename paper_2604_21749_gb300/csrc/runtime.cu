@@ -1176,19 +1176,26 @@ curast_status curast_autotune(curast_ctx *c, const curast_view *views, int n_vie
     float best_ms = 1e30f;
     bool exact = true;
     if (st == CURAST_OK) st = measure(base, &best_ms, &exact);
-    // coordinate descent over the batch shape, the two stage thresholds and the tile size
+    // coordinate descent over the batch shape, the two stage thresholds, the
+    // tile size, the pairs a work item loops over and the group test's
+    // threshold (none of them changes the buffer; a candidate that did would
+    // be rejected below)
     const uint32_t tpts[] = {1, 2, 4};
     const uint32_t s1s[] = {32, 64, 128, 256};
     const uint32_t s2s[] = {1024, 4096, 16384};
     const uint32_t tiles[] = {5, 6, 7};
-    for (int dim = 0; dim < 4 && st == CURAST_OK; ++dim) {
-        const int n = dim == 0 ? 3 : dim == 1 ? 4 : dim == 2 ? 3 : 3;
+    const uint32_t ppss[] = {16, 32, 64};
+    const uint32_t groups[] = {0, 2, 8};
+    for (int dim = 0; dim < 6 && st == CURAST_OK; ++dim) {
+        const int n = dim == 1 ? 4 : 3;
         for (int k = 0; k < n && st == CURAST_OK; ++k) {
             curast_config cand = best;
             if (dim == 0) cand.stage1_tri_per_thread = tpts[k];
             if (dim == 1) cand.stage1_max_pixels = s1s[k];
             if (dim == 2) cand.stage2_max_pixels = s2s[k];
             if (dim == 3) cand.tile_log2 = tiles[k];
+            if (dim == 4) cand.pairs_per_segment = ppss[k];
+            if (dim == 5) cand.stage1_group_min_pairs = groups[k];
             if (std::memcmp(&cand, &best, sizeof(cand)) == 0) continue;
             float ms = 0.0f;
             bool ok = false;
