@@ -49,6 +49,8 @@ def parse_args():
                    help="skip the 2x2 / 4x4 super-sampled frames")
     p.add_argument("--no-compressed", dest="compressed", action="store_false",
                    help="skip the frame with compressed geometry")
+    p.add_argument("--no-diff", dest="diff", action="store_false",
+                   help="skip the differentiable interpolation step (forward and backward)")
     p.add_argument("--no-raycast", dest="raycast", action="store_false",
                    help="skip the stage-3 workloads timed with the fixed-point rule and with the ray cast")
     p.add_argument("--subset", type=int, default=0,
@@ -374,6 +376,8 @@ def run_ours(args, ranks: Ranks):
 
     if ranks.rank == 0 and ranks.world == 1 and args.raycast:
         result["raycast_stage3"] = raycast_stage3(args, dev)
+    if ranks.rank == 0 and ranks.world == 1 and args.diff:
+        result["differentiable"] = differentiable_step(dev)
     if ranks.rank == 0 and ranks.world == 1 and args.batched != "off":
         result["batched_vs_plain"] = batched_vs_plain(args, dev)
     if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
@@ -454,6 +458,45 @@ def supersampling(r, cam, args, ms_1x1, stream):
         out[f"{ss}x{ss}_resolve_ms"] = round(e1.elapsed_time(e2), 3)
         del vis
         torch.cuda.empty_cache()
+    return out
+
+
+def differentiable_step(dev):
+    """The differentiable workload (1448^2-cell heightfield, 1024^2, FP32 RGB
+    per-vertex colours): with the visibility buffer fixed, the interpolation
+    forward (image from colours) and backward (colour and position gradients
+    from an image gradient) through the public API, ms per call."""
+    import torch
+    import synthetic as S
+    from paper_2604_21749_gb300 import api
+    sc, col = S.scene_differentiable(device=dev)
+    m, cam = sc.meshes[0], sc.cameras[0]
+    r = api.Renderer(dev.index)
+    r.upload_mesh(m.pos, m.idx, m.rgba8)
+    r.add_instance(0, sc.instances[0].model)
+    vis = r.render(cam.view, cam.proj, cam.W, cam.H)
+    col = col.to(dev).contiguous()
+    g = torch.randn((cam.H, cam.W, 3), generator=torch.Generator(device=dev).manual_seed(7), device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"differentiable: {m.T} triangles, {cam.W}x{cam.H}, RGB FP32 per-vertex colours"}
+    for name, fn in (("forward", lambda: r.interpolate(0, cam.view, cam.proj, vis, col, pos=m.pos)),
+                     ("backward", lambda: r.interpolate_backward(0, cam.view, cam.proj, vis, col, g, pos=m.pos))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name + "_ms"] = round(ms, 4)
+        out[name + "_mpix_s"] = round(cam.W * cam.H / (ms * 1e-3) / 1e6, 1)
+    r.close()
+    del vis, g
+    torch.cuda.empty_cache()
     return out
 
 
