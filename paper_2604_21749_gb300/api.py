@@ -206,6 +206,10 @@ class Renderer:
         return c
 
     def set_config(self, **kw) -> Config:
+        known = {k for k, _ in Config._fields_}
+        for k in kw:
+            if k not in known:
+                raise KeyError(f"unknown config field {k!r}")
         c = self.config
         for k, v in kw.items():
             setattr(c, k, v)

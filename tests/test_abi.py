@@ -63,3 +63,42 @@ def test_renderer_refuses_without_gpu():
     from paper_2604_21749_gb300 import api
     with pytest.raises(RuntimeError):
         api.Renderer(0)
+
+
+_STRUCTS = {"View": "curast_view", "Config": "curast_config", "Stats": "curast_stats",
+            "MeshInfo": "curast_mesh_info", "FrameInfo": "curast_frame_info"}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and the field
+    offsets the C compiler gives the header's struct."""
+    import subprocess
+    from paper_2604_21749_gb300 import api
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "curast.h"', "int main(void) {"]
+    for py, c in _STRUCTS.items():
+        lines.append(f'    printf("{py} size %zu\\n", sizeof({c}));')
+        for name, _ in getattr(api, py)._fields_:
+            lines.append(f'    printf("{py} {name} %zu\\n", offsetof({c}, {name}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            py, name, v = ln.split()
+            got[(py, name)] = int(v)
+    for py in _STRUCTS:
+        cls = getattr(api, py)
+        assert got[(py, "size")] == ctypes.sizeof(cls), py
+        for name, _ in cls._fields_:
+            assert got[(py, name)] == getattr(cls, name).offset, (py, name)
+
+
+def test_set_config_rejects_unknown_keys():
+    from paper_2604_21749_gb300 import api
+    r = object.__new__(api.Renderer)
+    with pytest.raises(KeyError):
+        api.Renderer.set_config(r, stage3_raycats=1)
