@@ -49,6 +49,8 @@ def parse_args():
                    help="skip the 2x2 / 4x4 super-sampled frames")
     p.add_argument("--no-compressed", dest="compressed", action="store_false",
                    help="skip the frame with compressed geometry")
+    p.add_argument("--no-ablation", dest="ablation", action="store_false",
+                   help="skip the frame without the conservative cull (every triangle on the exact path)")
     p.add_argument("--no-diff", dest="diff", action="store_false",
                    help="skip the differentiable interpolation step (forward and backward)")
     p.add_argument("--no-raycast", dest="raycast", action="store_false",
@@ -368,6 +370,8 @@ def run_ours(args, ranks: Ranks):
     }
     if ranks.rank == 0 and ranks.world == 1 and args.supersampling:
         result["supersampling"] = supersampling(r, cam, args, ms_frame, stream)
+    if ranks.rank == 0 and ranks.world == 1 and args.ablation:
+        result["conservative_cull"] = conservative_cull_ablation(r, cam, args, ms_frame, vis, stream)
     r.close()
     if ranks.rank == 0 and ranks.world == 1 and args.compressed:
         result["compressed"] = compressed_frame(args, sc, cam, dev, stream, info, ms_frame)
@@ -431,6 +435,32 @@ def compressed_frame(args, sc, cam, dev, stream, info_plain, ms_plain):
             "uncompressed_bytes_read": round(plain_bytes),
             "cull_gbs": round(read_bytes / (cull_ms * 1e-3) / 1e9, 1),
             "triangles_per_frame": info["triangles"]}
+
+
+def conservative_cull_ablation(r, cam, args, ms_on, vis, stream):
+    """The paper's Table 4 on this frame: the same frame with the conservative
+    tiny-triangle cull off (stage1_exact_all), so that every (triangle, pair)
+    takes the exact path, which drops tiny and off-screen triangles itself.
+    The buffer is the same; frame ms and stage ms of that frame."""
+    import torch
+    r.set_config(stage1_exact_all=1)
+    r.render(cam.view, cam.proj, args.W, args.H, vis)
+    r.sync()
+    frames = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(frames):
+        r.render(cam.view, cam.proj, args.W, args.H, vis)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_off = e0.elapsed_time(e1) / frames
+    r.render(cam.view, cam.proj, args.W, args.H, vis)
+    st = r.stage_times()
+    r.set_config(stage1_exact_all=0)
+    return {"frame_ms_without": round(ms_off, 3), "frame_ms_with": round(ms_on, 3),
+            "speedup": round(ms_off / ms_on, 2),
+            "stage_ms_without": {k: round(v, 3) for k, v in
+                                 zip(["clear", "stage1_cull", "stage1_exact", "stage2", "stage3"], st)}}
 
 
 def supersampling(r, cam, args, ms_1x1, stream):

@@ -101,6 +101,12 @@ typedef struct {
                                     pixel-centre rays instead of the fixed-point rule (the
                                     result then follows the ray-cast reading, not the
                                     default one); 0 (default): one fixed-point rule for all */
+    uint32_t stage1_exact_all;   /* 1: no conservative cull in stage 1 -- every (triangle,
+                                    pair) takes the exact path, which culls tiny and
+                                    off-screen triangles itself (the result is the same;
+                                    for measuring what the conservative cull saves);
+                                    0 (default)                                              */
+    uint32_t reserved;           /* 0                                                        */
 } curast_config;
 
 /* Counters read back by curast_sync.  Stats fields are filled only when

@@ -48,7 +48,8 @@ class Config(C.Structure):
                 ("stage1_tri_per_thread", C.c_uint32), ("pairs_per_segment", C.c_uint32),
                 ("queue1_capacity", C.c_uint64), ("queue2_capacity", C.c_uint64), ("check_indices", C.c_uint32),
                 ("collect_stats", C.c_uint32), ("stage1_bitmap_bytes", C.c_uint64),
-                ("stage1_group_min_pairs", C.c_uint32), ("stage3_raycast", C.c_uint32)]
+                ("stage1_group_min_pairs", C.c_uint32), ("stage3_raycast", C.c_uint32),
+                ("stage1_exact_all", C.c_uint32), ("reserved", C.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -405,6 +405,7 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
                 p.view = (uint32_t)v;
                 p.mesh = (uint32_t)m;
                 fast_constants(p, mr, c->hv[v]);
+                if (c->cfg.stage1_exact_all) p.wsafe = INFINITY;   // the conservative cull never applies
                 c->hp.push_back(p);
             }
         }
@@ -762,7 +763,7 @@ bool valid_config(const curast_config &c) {
            c.pairs_per_segment >= 1 && c.pairs_per_segment <= 64 && c.queue1_capacity >= 1 &&
            c.queue2_capacity >= 1 && c.queue1_capacity <= (1ull << 32) && c.queue2_capacity <= (1ull << 32) &&
            c.stage1_bitmap_bytes >= (1ull << 12) && c.stage1_bitmap_bytes <= (1ull << 36) &&
-           c.stage1_group_min_pairs <= 64 && c.stage3_raycast <= 1;
+           c.stage1_group_min_pairs <= 64 && c.stage3_raycast <= 1 && c.stage1_exact_all <= 1 && c.reserved == 0;
 }
 
 }  // namespace

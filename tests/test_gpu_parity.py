@@ -61,6 +61,7 @@ def test_small_workload_bit_exact_and_resolve(api, small):
     dict(stage1_tri_per_thread=1), dict(stage1_tri_per_thread=3),
     dict(queue1_capacity=1, queue2_capacity=1), dict(queue1_capacity=7, queue2_capacity=3),
     dict(stage1_bitmap_bytes=1 << 12), dict(stage1_bitmap_bytes=1 << 12, stage1_tri_per_thread=1),
+    dict(stage1_exact_all=1), dict(stage1_exact_all=1, stage1_bitmap_bytes=1 << 12),
 ])
 def test_stage_choices_never_change_visibility(api, small, cfg):
     """Thresholds, tile size, batch shape and queue overflow move triangles
@@ -126,12 +127,13 @@ def mixed():
     return _mixed_scene()
 
 
-@pytest.mark.parametrize("use_graph,bitmap", [(False, 1 << 30), (True, 1 << 30), (True, 1 << 12)])
-def test_batched_views_equal_oracle(api, mixed, use_graph, bitmap):
+@pytest.mark.parametrize("use_graph,bitmap,exact_all", [(False, 1 << 30, 0), (True, 1 << 30, 0), (True, 1 << 12, 0),
+                                                        (True, 1 << 30, 1)])
+def test_batched_views_equal_oracle(api, mixed, use_graph, bitmap, exact_all):
     """Many meshes, rotated/scaled instances (some culled), an empty mesh and
     three views of different sizes in one batched launch (graph or not; one
-    stage-1 round or several)."""
-    r = _renderer(api, pairs_per_segment=7, stage1_bitmap_bytes=bitmap)
+    stage-1 round or several; with or without the conservative cull)."""
+    r = _renderer(api, pairs_per_segment=7, stage1_bitmap_bytes=bitmap, stage1_exact_all=exact_all)
     keep = upload(r, mixed)
     views = [(c.view, c.proj, c.W, c.H, None) for c in mixed.cameras]
     for frame in range(2):   # the second frame replays the captured graph
