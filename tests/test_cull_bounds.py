@@ -88,6 +88,19 @@ def _setups():
         out.append((cam, model, lo, hi, f"billion tile {tx},{tz}"))
     for k in (0, 3, 6):
         out.append((S.camera_unique_pose(k, 1920, 1080), np.eye(4, dtype=np.float32), lo, hi, f"unique pose {k}"))
+    # extremes: a tiny near plane with the mesh far away, and a huge instance seen from afar
+    # (large row magnitudes, so wsafe is raised well above near)
+    cam = S.Camera(S.look_at((0.5, 0.3, -0.2), (0.5, 0.0, 0.6)), S.perspective(70.0, 16 / 9, 1e-3, 100.0), 1920, 1080)
+    far = np.eye(4, dtype=np.float32)
+    far[:3, 3] = (0.0, 0.0, 40.0)
+    out.append((cam, far, lo, hi, "tiny near, far mesh"))
+    big = np.eye(4)
+    big[:3, :3] = S.scenes._random_rotation(rng) * 1000.0
+    big[:3, 3] = (-300.0, -10.0, -300.0)
+    centre = big[:3, :3] @ np.array([0.5, 0.0, 0.5]) + big[:3, 3]
+    out.append((S.Camera(S.look_at(tuple(centre + np.array([0.0, 700.0, -1200.0])), tuple(centre)),
+                         S.perspective(60.0, 16 / 9, 0.05, 5000.0), 3840, 2160),
+                big.astype(np.float32), lo, hi, "instance of scale 1000"))
     for k, (W, H) in enumerate(((640, 360), (3840, 2160), (1920, 1080))):
         ang = rng.uniform(0, 2 * np.pi)
         eye = (140 * math.cos(ang), 70.0, 140 * math.sin(ang))
