@@ -37,6 +37,7 @@ C_MUTATIONS = [
     ("clip, t from the outside value", "    float t = fin / den;", "    float t = fout / den;"),
     ("clip, left guard sign", "return v.x + ORC_GUARD * v.w;", "return v.x - ORC_GUARD * v.w;"),
     ("snap, truncation", "*X = (int32_t)rintf(xs);", "*X = (int32_t)xs;"),
+    ("snap, ties away from zero", "*Y = (int32_t)rintf(ys);", "*Y = (int32_t)roundf(ys);"),
     ("screen, y down", "float py = sy + 1.0f;", "float py = 1.0f - sy;"),
     ("edge function reversed", "int64_t E1 = edge(X[2], Y[2], X[0], Y[0], px, py);",
      "int64_t E1 = edge(X[0], Y[0], X[2], Y[2], px, py);"),
@@ -50,6 +51,9 @@ C_MUTATIONS = [
     ("resolve, pixel centre", "float ndx = ((float)(2 * x + 1) / (float)cam->W) - 1.0f;",
      "float ndx = ((float)(2 * x) / (float)cam->W) - 1.0f;"),
     ("interpolation, wrong colour index", "    float q = b[1] * c1;", "    float q = b[1] * c2;"),
+    ("resolve, upper clamp of RGBA8 dropped",
+     "                    float c = out[ch];\n                    if (!(c >= 0.0f)) c = 0.0f;\n                    if (c > 1.0f) c = 1.0f;",
+     "                    float c = out[ch];\n                    if (!(c >= 0.0f)) c = 0.0f;"),
     ("box filter, divides by ss", "    const float n = (float)(ss * ss);", "    const float n = (float)(ss);"),
     ("box filter, wrong sample row", "size_t f = (size_t)(ss * y + sy) * (size_t)Wf", "size_t f = (size_t)(ss * y + sx) * (size_t)Wf"),
     ("index bits, log2 of the span", "((uint64_t)1 << b) < (uint64_t)span + 1", "((uint64_t)1 << b) < (uint64_t)span"),

@@ -474,6 +474,24 @@ def test_resolve_constant_colour_and_background(oracle_lib):
                                atol=1e-6)
 
 
+def test_resolve_rgba8_clamps_extrapolated_colours(oracle_lib):
+    """The resolve's barycentrics are not clamped (Section 4.4 extrapolates
+    outside the triangle for mip levels): a buffer that names one small
+    triangle at every pixel gives FP32 colours far outside [0, 1] away from
+    it, and RGBA8 is rint(clamp(c, 0, 1) * 255) of those FP32 colours."""
+    O = oracle_lib
+    pos = [[-0.1, -0.1, -2.0], [0.1, -0.1, -2.0], [0.0, 0.1, -2.0]]
+    col = [[255, 0, 128, 255], [0, 255, 0, 255], [0, 0, 255, 255]]
+    sc = Scene([mesh_np(pos, [[0, 1, 2]], col)], [Instance(0, ident())])
+    cam = _cam(np.eye(4), S.perspective(60, 1.0, 0.01, 10.0), 40, 40)
+    osc = O.OracleScene(sc)
+    vis = np.full((40, 40), np.uint64(1 << 36), np.uint64)             # triangle 0 everywhere
+    rgba, rgba8 = O.resolve(osc, cam, vis)
+    assert (rgba > 1.01).any() and (rgba < -0.01).any()
+    want = np.rint(np.clip(rgba.astype(np.float64), 0.0, 1.0) * 255.0).astype(np.uint8)
+    np.testing.assert_array_equal(rgba8, want)
+
+
 def test_ids_follow_prefix_sum_with_empty_instances(oracle_lib):
     """Id = base[instance] + triangle; zero-triangle instances share their
     base with the successor and never capture a pixel in the resolve."""
@@ -789,3 +807,22 @@ def test_paper_stage3_routing_thresholds(oracle_lib):
     ray = O.render_paper(osc, cam, s1_max=128, s2_max=K - 1)
     assert (O.decode(ray)[0] != O.decode(edge)[0]).any()
     np.testing.assert_array_equal(O.render_paper(osc, cam, s1_max=K, s2_max=32), edge)
+
+
+def test_snap_ties_round_to_even(oracle_lib):
+    """R1 snaps with round-half-to-even: a vertex whose 256 X falls exactly
+    on k + 1/2 goes to the even neighbour (camera with fx = fy = 1, depth 1
+    and a 2 x 2 screen make 256 X = 256 (vx + 1) exact)."""
+    O = oracle_lib
+    cp = O.camera_params(S.perspective(90.0, 1.0, 0.01, 100.0))
+    assert tuple(cp[:2]) == (1.0, 1.0)
+    mv = np.eye(4, dtype=np.float32)[:3]
+    k = np.arange(250, 262)
+    for frac in (0.5, 0.25, 0.75):
+        v = ((k + frac) / 256.0 - 1.0).astype(np.float32)
+        assert np.array_equal((v.astype(np.float64) + 1.0) * 256.0, k + frac)      # the ties are exact
+        pts = np.stack([v, v[::-1], -np.ones_like(v)], 1).astype(np.float32)
+        _, XY, _, inside = O.project(mv, cp, 2, 2, pts)
+        assert inside.all()
+        np.testing.assert_array_equal(XY[:, 0], np.rint(k + frac))          # numpy rint: half to even
+        np.testing.assert_array_equal(XY[:, 1], np.rint(k[::-1] + frac))
