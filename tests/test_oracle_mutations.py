@@ -67,6 +67,8 @@ C_MUTATIONS = [
     ("ray cast, b0 from u twice", "            b0 = b0 - w;\n            float t", "            b0 = b0 - u;\n            float t"),
     ("ray cast, depth from e1", "float t = dot3(e2, qv) / det;", "float t = dot3(e1, qv) / det;"),
     ("ray cast routing, s2 threshold", "> (int64_t)s2_max) {", ">= (int64_t)s2_max) {"),
+    ("ray cast routing, extent rule dropped", "int large = mxx - mnx >= 16384 || mxy - mny >= 16384 ||",
+     "int large = 0 ||"),
 ]
 
 PY_MUTATIONS = [

@@ -807,6 +807,21 @@ def test_paper_stage3_routing_thresholds(oracle_lib):
     ray = O.render_paper(osc, cam, s1_max=128, s2_max=K - 1)
     assert (O.decode(ray)[0] != O.decode(edge)[0]).any()
     np.testing.assert_array_equal(O.render_paper(osc, cam, s1_max=K, s2_max=32), edge)
+    # a long thin triangle (76 centres, within s1_max) still leaves stage 1 for its 64-pixel
+    # extent, and with s2_max below its count it is ray cast
+    W2, H2 = 200, 60
+    proj2 = S.perspective(60, W2 / H2, 0.05, 100.0)
+    cam2 = _cam(np.eye(4), proj2, W2, H2)
+    fx2, fy2, nv2 = O.camera_params(proj2)
+    thin = np.array([[-2.6, -0.05, -3.2], [2.5, -0.035, -3.8], [0.1, 0.01, -3.5]], np.float32)
+    _, XY2, _, _ = O.project(np.eye(4, dtype=np.float32)[:3], np.array([fx2, fy2, nv2], np.float32), W2, H2, thin)
+    lo2 = np.maximum(-((128 - XY2.min(0).astype(np.int64)) // 256), 0)
+    hi2 = np.minimum((XY2.max(0).astype(np.int64) - 128) // 256, [W2 - 1, H2 - 1])
+    assert int((hi2[0] - lo2[0] + 1) * (hi2[1] - lo2[1] + 1)) <= 128 and XY2[:, 0].max() - XY2[:, 0].min() >= 1 << 14
+    osc2 = O.OracleScene(_tri_scene(thin))
+    edge2 = O.render(osc2, cam2)
+    assert (edge2 != O.EMPTY).sum() > 20
+    assert (O.decode(O.render_paper(osc2, cam2, s1_max=128, s2_max=32))[0] != O.decode(edge2)[0]).any()
 
 
 def test_snap_ties_round_to_even(oracle_lib):
