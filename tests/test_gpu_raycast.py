@@ -114,3 +114,21 @@ def test_batched_views_ray_cast(api, use_graph):
         for c, v in zip(sc.cameras, out):
             assert_vis_equal(v, _paper(sc, c, 128, 64), f"batched {c.W}x{c.H} frame {frame}")
     del keep
+
+
+def test_thin_triangle_routed_by_extent(api):
+    """A long thin triangle within stage 1's pixel limit leaves stage 1 for its
+    64-pixel extent and, past stage2_max_pixels, takes the ray cast."""
+    tri = np.array([[-2.6, -0.05, -3.2], [2.5, -0.035, -3.8], [0.1, 0.01, -3.5]], np.float32)
+    m = S.Mesh(pos=torch.tensor(tri), idx=torch.tensor([[0, 1, 2]], dtype=torch.int32), rgba8=None)
+    sc = Scene([m], [Instance(0, np.eye(4, dtype=np.float32))], [])
+    cam = S.Camera(np.eye(4, dtype=np.float32), S.perspective(60, 200 / 60, 0.05, 100.0), 200, 60)
+    r = _renderer(api, stage2_max_pixels=32)
+    keep = upload(r, sc, with_colour=False)
+    vis = r.render(cam.view, cam.proj, cam.W, cam.H)
+    r.sync()
+    ref = _paper(sc, cam, 128, 32)
+    assert (ref != orc.EMPTY).sum() > 20
+    assert_vis_equal(vis, ref, "thin triangle")
+    assert (ref != orc.render(orc.OracleScene(sc), cam)).any()
+    del keep
