@@ -43,9 +43,9 @@
  *   R5 ids are numbered over all instances, culled or not;
  *   R6 ties in depth28 go to the smaller id (64-bit minimum).
  *
- * Parity unpinned: a point on the near plane takes w = near exactly rather
- * than its interpolated w.  The two differ by rounding only and no pin
- * separates them; every other step is pinned by tests/test_oracle_pins.py.
+ * Every step is pinned by tests/test_oracle_pins.py; among them, a point cut
+ * by the near plane takes w = near exactly, the w of every point of that
+ * plane (the interpolated w would carry rounding).
  */
 #include <math.h>
 #include <stdint.h>

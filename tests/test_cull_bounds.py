@@ -10,7 +10,8 @@ rounding bounds) and the kernels' FP32 arithmetic in numpy, sample vertices
 and small vertex groups under the bench cameras and random instance
 transforms, and check that the exact positions never leave the widened
 ranges: the worst excursion must stay below the margin.  rcp.approx is
-modelled with a relative error of 2^-22 either way (the bound assumes 2^-20).
+modelled with a relative error of 2^-20 either way, the error the margins
+are derived for (8 times the documented bound of the instruction).
 """
 import math
 
@@ -37,8 +38,9 @@ def _fma(a, b, c):
 
 
 def _rcp(x, s):
-    """rcp.approx modelled as the exact reciprocal off by 2^-22 relative."""
-    return _f32(1.0 / np.asarray(x, F32).astype(np.float64) * (1.0 + s * 2.0 ** -22))
+    """rcp.approx modelled as the exact reciprocal off by RHO = 2^-20
+    relative, the error the host's margins assume, in direction s."""
+    return _f32(1.0 / np.asarray(x, F32).astype(np.float64) * (1.0 + s * RHO))
 
 
 def _constants(mv, lo, hi, cp, W, H):

@@ -3,10 +3,7 @@
 Every case copies the oracle into a scratch directory, plants one mistake
 (a flipped sign, a dropped term, a transposed operand, a wrong index, an off
 by one), and runs the pins of test_oracle_pins.py against the copy on the
-CPU.  A mistake the pins do not notice fails this test.  The one known
-survivor -- whether a near-plane intersection takes w = near exactly or the
-interpolated w, a rounding-level choice no geometric fact separates -- is the
-only part of the oracle left unpinned.
+CPU.  A mistake the pins do not notice fails this test.
 """
 import concurrent.futures as cf
 import os
@@ -67,6 +64,8 @@ C_MUTATIONS = [
     ("ray cast, b0 from u twice", "            b0 = b0 - w;\n            float t", "            b0 = b0 - u;\n            float t"),
     ("ray cast, depth from e1", "float t = dot3(e2, qv) / det;", "float t = dot3(e1, qv) / det;"),
     ("ray cast routing, s2 threshold", "> (int64_t)s2_max) {", ">= (int64_t)s2_max) {"),
+    ("clip, near-plane w interpolated", "    if (p == 0) r.w = nearv;\n    else if (r.w < nearv) r.w = nearv;",
+     "    if (r.w < nearv) r.w = nearv;"),
     ("ray cast routing, extent rule dropped", "int large = mxx - mnx >= 16384 || mxy - mny >= 16384 ||",
      "int large = 0 ||"),
 ]
@@ -116,10 +115,3 @@ def test_planted_mistakes_fail_a_pin(tmp_path):
         results = [f.result() for f in futs]
     bad = [f"{name}: {why}" for name, why in results if why is not None]
     assert not bad, "\n".join(bad)
-
-
-def test_unpinned_near_plane_w_is_known():
-    """The near-plane w choice is the documented unpinned detail; keep the
-    planted-mistake list honest by checking the site still exists."""
-    src = open(os.path.join(ROOT, "oracle", "curast_oracle.c")).read()
-    assert src.count("if (p == 0) r.w = nearv;") == 1

@@ -409,6 +409,33 @@ def test_clip_polygon_properties(oracle_lib):
             assert (bary > -1e-3).all() and (bary < 1 + 1e-3).all()
 
 
+def test_near_plane_cut_lies_on_the_plane(oracle_lib):
+    """The point where an edge meets the near plane w = near has w = near
+    exactly (Section 4.2 clips against the near plane; the intersection is a
+    point of the plane).  x and y come from the FP32 interpolation and carry
+    its rounding, but w is fixed by the geometry: every vertex the near cut
+    creates must hold w == near bit for bit.  Triangles are kept well inside
+    the guard band, so the near plane is the only cut."""
+    O = oracle_lib
+    rng = np.random.default_rng(29)
+    nearv = np.float32(0.05)
+    created = 0
+    for _ in range(400):
+        w = rng.uniform(-1.0, 2.0, 3)
+        if (w >= nearv).all() or (w < nearv).all():
+            continue
+        xy = rng.uniform(-0.1, 0.1, (3, 2))
+        tri = np.concatenate([xy, w[:, None]], 1).astype(np.float32)
+        poly = O.clip(tri, nearv)
+        assert len(poly) in (3, 4)
+        for v in poly:
+            if any(np.array_equal(v, t) for t in tri):
+                continue
+            created += 1
+            assert v[2] == nearv, f"near cut at w = {v[2]!r}, not {nearv!r}"
+    assert created > 200
+
+
 def test_shared_edges_clip_watertight(oracle_lib):
     """Random triangle pairs sharing an edge that crosses the near plane and
     the guard band never double-cover a sample."""
