@@ -316,9 +316,10 @@ curast_status curast_autotune(curast_ctx *ctx, const curast_view *views, int n_v
 /* ------------------------------------------------- no-allocation render --- */
 
 /* The paper has no counterpart of this call; it exists for callers that
- * cannot allocate device memory -- code running while a CUDA graph is being
- * captured, real-time loops that must not allocate, hosts that hand out
- * device memory only from their own pools.
+ * cannot allocate device memory -- real-time loops that must not allocate
+ * (an allocation may synchronize the device and take milliseconds), and
+ * plug-ins whose host hands out device memory only from its own pools or
+ * reserves all of it up front.
  *
  * Renders n_instances (1..CURAST_STATIC_MAX_INSTANCES) instances of one mesh
  * into one view, like curast_render with the same mesh and instances, and
@@ -331,14 +332,20 @@ curast_status curast_autotune(curast_ctx *ctx, const curast_view *views, int n_v
  * The pipeline's scratch (frame tables, counters, stage queues) is one fixed
  * array of about 2 MB in the library's device memory, which every GPU that
  * loads the library holds until the process exits.  Consequences:
- *   - the first call on a device looks the array's address up (and sets the
- *     kernels' shared-memory limits); make that first call before any stream
- *     capture;
+ *   - the first call on a device (with that device current) looks the
+ *     array's address up and sets the kernels' shared-memory limits; make
+ *     that first call before any stream capture; if it fails, the next call
+ *     tries again;
  *   - every call uses the same array and leaves its contents behind (the
  *     counters are cleared at the start of each call): calls that overlap on
  *     the GPU -- on two streams, or from two host threads -- race and corrupt
  *     each other's frames; serialize them;
- *   - indices >= V are skipped but not reported (no context to latch them);
+ *   - indices >= V are skipped but not reported (no context to latch them),
+ *     and neither is a bounded wait of the stage-1 kernel that gave up (its
+ *     triangles are then missing from the frame) -- the call still returns
+ *     CURAST_OK;
+ *   - the call works on the current CUDA device, which must hold pos, idx,
+ *     vis and the stream;
  *   - the stage-1 cull runs its exact path for every triangle (no mesh
  *     bounds are computed), so it is slower than curast_render.
  * Fails with CURAST_ERR_TOO_LARGE for n_instances outside 1..32 or V, T at

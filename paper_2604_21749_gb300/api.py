@@ -383,23 +383,40 @@ def render_static(pos: torch.Tensor, idx: torch.Tensor, models, view, proj, W: i
                   vis: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """Context-free render of up to 32 instances of one mesh that allocates no
     device memory in the library (curast_render_static): for callers that must
-    not allocate, e.g. while a CUDA graph is being captured.  ``models`` is a
-    sequence of 4x4 matrices or None (one identity instance).  All calls share
-    one fixed scratch array, so calls must not overlap on the GPU; the first
-    call on a device should happen before any stream capture."""
+    not allocate, such as real-time loops or plug-ins whose host owns all
+    device memory.  ``models`` is a sequence of 4x4 matrices or None (one
+    identity instance).  All calls share one fixed scratch array, so calls
+    must not overlap on the GPU; the first call on a device should happen
+    before any stream capture.  pos, idx and vis must live on one device; the
+    call runs with that device current."""
     L = load()
-    if not (pos.is_cuda and idx.is_cuda and pos.dtype == torch.float32 and pos.is_contiguous() and idx.is_contiguous()):
-        raise ValueError("pos must be a contiguous CUDA float32 tensor and idx a contiguous CUDA uint32 tensor")
+    dev = pos.device if isinstance(pos, torch.Tensor) else None
+    if dev is None or dev.type != "cuda":
+        raise ValueError("pos must be a contiguous CUDA float32 tensor")
+    _need(pos, torch.float32, "pos", dev)
+    if not isinstance(idx, torch.Tensor) or idx.dtype not in (torch.int32, torch.uint32):
+        raise ValueError("idx must hold uint32 (int32 tensor)")
+    _need(idx, idx.dtype, "idx", dev)
+    if pos.dim() != 2 or pos.shape[1] != 3 or idx.dim() != 2 or idx.shape[1] != 3:
+        raise ValueError("pos must be (V, 3) and idx (T, 3)")
     if vis is None:
-        vis = torch.empty((H, W), dtype=torch.int64, device=pos.device)
+        vis = torch.empty((H, W), dtype=torch.int64, device=dev)
+    _need(vis, torch.int64, "vis", dev)
+    if vis.numel() != W * H:
+        raise ValueError("vis must hold W*H words")
     if models is None:
         mats, n = None, 1
     else:
         arr = np.ascontiguousarray(np.stack([np.asarray(m, np.float32).reshape(16) for m in models]), np.float32)
         n = arr.shape[0]
         mats = (C.c_float * (16 * n))(*[float(x) for x in arr.reshape(-1)])
-    _check(L.curast_render_static(_ptr(pos), pos.shape[0], _ptr(idx), idx.shape[0], mats, n, _mat(view), _mat(proj),
-                                  W, H, _ptr(vis), _stream(stream)), "curast_render_static")
+    with torch.cuda.device(dev):
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        if st.device != dev:
+            raise ValueError(f"the stream is on {st.device}, the buffers on {dev}")
+        _check(L.curast_render_static(_ptr(pos), pos.shape[0], _ptr(idx), idx.shape[0], mats, n, _mat(view),
+                                      _mat(proj), W, H, _ptr(vis), C.c_void_p(st.cuda_stream)),
+               "curast_render_static")
     return vis
 
 

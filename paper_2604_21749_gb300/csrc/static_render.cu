@@ -1,13 +1,13 @@
 // static_render.cu -- curast_render_static: the rasterizer for callers that
 // must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation is not a stream operation), real-time loops
-// that are not allowed to allocate, and hosts that hand out device memory
-// only through their own pools.  This entry point renders up to
-// kStaticMaxInstances instances of one mesh into one view with no context
-// and no allocation: every buffer the pipeline needs besides the caller's
-// inputs and outputs (frame tables, counters, the stage-1 -> 2 and
+// Some callers cannot call cudaMalloc: real-time loops that are not allowed
+// to allocate (an allocation can synchronize the device and take
+// milliseconds), and plug-ins whose host hands out device memory only
+// through its own pools or reserves all of it up front.  This entry point
+// renders up to kStaticMaxInstances instances of one mesh into one view with
+// no context and no allocation: every buffer the pipeline needs besides the
+// caller's inputs and outputs (frame tables, counters, the stage-1 -> 2 and
 // stage-2 -> 3 queues) lives in one file-scope __device__ array.
 #include <cmath>
 #include <cstring>
@@ -84,29 +84,37 @@ __global__ void k_static_setup(StaticFrame s) {
 }
 
 // Per-device set-up: the scratch's device address and the launch shape.
+// It is marked done only when it succeeded, so a failed first call (a
+// transient error) is retried by the next call instead of failing every
+// later call on that device.
 struct DeviceSetup {
-    std::once_flag once;
-    cudaError_t status = cudaSuccess;
+    bool done = false;
     unsigned char *scratch = nullptr;
     LaunchShape shape{};
 };
 constexpr int kMaxDevices = 64;
 DeviceSetup g_setup[kMaxDevices];
+std::mutex g_setup_mutex;
 
 // In host code g_static_scratch names a host-side stand-in, not device
 // memory: the kernels get the address cudaGetSymbolAddress returns for the
 // current device.
 cudaError_t device_setup(int dev, DeviceSetup **out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup &d = g_setup[dev];
-    std::call_once(d.once, [&d, dev]() {
+    if (!d.done) {
         void *p = nullptr;
-        d.status = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (d.status == cudaSuccess) d.scratch = static_cast<unsigned char *>(p);
-        if (d.status == cudaSuccess) d.status = query_launch_shape(&d.shape, dev);
-    });
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        LaunchShape sh{};
+        if ((e = query_launch_shape(&sh, dev)) != cudaSuccess) return e;
+        d.scratch = static_cast<unsigned char *>(p);
+        d.shape = sh;
+        d.done = true;
+    }
     *out = &d;
-    return d.status;
+    return cudaSuccess;
 }
 
 bool affine_static(const float *m) { return m && m[12] == 0.0f && m[13] == 0.0f && m[14] == 0.0f && m[15] == 1.0f; }

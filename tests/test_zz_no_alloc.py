@@ -1,7 +1,7 @@
 """curast_render_static -- the render for callers that cannot allocate device
-memory (for example code running while a CUDA graph is being captured) --
-must give the same visibility buffers as the context API, call after call,
-even though all its calls share one fixed scratch array.
+memory (real-time loops that must not allocate, plug-ins whose host owns all
+device memory) -- must give the same visibility buffers as the context API,
+call after call, even though all its calls share one fixed scratch array.
 
 This file is collected last on purpose: it needs nothing from the other
 tests and passes on its own in a fresh process as well as after them.
@@ -69,3 +69,45 @@ def test_static_render_single_instance_and_limit():
     with pytest.raises(api.CurastError) as e:
         api.render_static(pos, idx, [np.eye(4)] * (api.STATIC_MAX_INSTANCES + 1), cam.view, cam.proj, 8, 8)
     assert e.value.status == -10
+
+
+def test_static_render_stages_2_3_and_queue_overflow():
+    """A camera inside nested closed boxes at 3840 x 2160: every face crosses
+    the near plane or the guard band, so stage 2 clips it and stage 3 gets
+    tens of thousands of tile parts -- more than the static path's queue 2
+    holds (16,384), so its overflow path rasterizes the rest in place.  The
+    context renderer, run with the static path's capacities and counters on,
+    shows that the workload takes those paths; the static render must still
+    equal the context render bit for bit, twice in a row."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_2604_21749_gb300 import api
+
+    room = S.scene_room()
+    mesh = room.meshes[0]
+    pos, idx = mesh.pos.cuda(), mesh.idx.cuda()
+    models = []
+    for k in range(6):
+        m = np.eye(4, dtype=np.float32)
+        m[:3, :3] *= np.float32(1.0 + 0.15 * k)
+        models.append(m)
+    cam = S.Camera(room.cameras[0].view, S.perspective(80, 3840 / 2160, 0.05, 100.0), 3840, 2160)
+    probe = api.Renderer(0)
+    probe.set_config(queue1_capacity=1 << 16, queue2_capacity=1 << 14, collect_stats=1)
+    probe.upload_mesh(pos, idx)
+    for m in models:
+        probe.add_instance(0, m)
+    probe.render(cam.view, cam.proj, cam.W, cam.H)
+    st = probe.sync()
+    assert st["queued_stage2"] > 0 and st["queued_stage3"] > 0 and st["queue2_overflow"] > 0, st
+    r = api.Renderer(0)
+    r.upload_mesh(pos, idx)
+    for m in models:
+        r.add_instance(0, m)
+    want = r.render(cam.view, cam.proj, cam.W, cam.H)
+    r.sync()
+    assert (want != -1).all()
+    for _ in range(2):
+        got = api.render_static(pos, idx, models, cam.view, cam.proj, cam.W, cam.H)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want)
