@@ -26,7 +26,10 @@
  *   - backface culling (Section 4.1);
  *   - the resolve pass: binary search of the prefix sum, per-pixel
  *     barycentrics of the pixel ray and the triangle in view space, and
- *     vertex-colour interpolation (Section 4.4).
+ *     vertex-colour interpolation (Section 4.4);
+ *   - the textured resolve: the mip level from the texture-space footprint
+ *     of four pixel rays, and the nearest texel of that level (Section 4.4
+ *     "Shading and Mip Mapping"; reading R17 below).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   R1 coverage is exact integer arithmetic on vertices snapped to 1/256 px,
@@ -41,7 +44,10 @@
  *      space ray cast is replaced by the same fixed-point rule); the ray
  *      cast itself is orc_render_paper at the end of this file (R16);
  *   R5 ids are numbered over all instances, culled or not;
- *   R6 ties in depth28 go to the smaller id (64-bit minimum).
+ *   R6 ties in depth28 go to the smaller id (64-bit minimum);
+ *   R17 the footprint is the larger side of the uv bounding box of the four
+ *      samples in level-0 texels, the level floor(log2) of it clamped to the
+ *      chain, and the texel the nearest one at the pixel's own uv.
  *
  * Every step is pinned by tests/test_oracle_pins.py; among them, a point cut
  * by the near plane takes w = near exactly, the w of every point of that
@@ -456,6 +462,26 @@ static uint64_t upper_bound_u64(const uint64_t *a, int n, uint64_t key)
     return (uint64_t)lo;
 }
 
+/* Barycentrics of the ray through the centre of pixel (x, y) -- which may
+ * lie just outside the screen -- with the triangle whose view-space
+ * vertices are v (camera at the origin; Moeller-Trumbore form, unclamped). */
+static void ray_bary(const float v[3][3], const orc_camera *cam, const float cp[3], int x, int y, float b[3])
+{
+    float ndx = ((float)(2 * x + 1) / (float)cam->W) - 1.0f;
+    float ndy = ((float)(2 * y + 1) / (float)cam->H) - 1.0f;
+    float r[3] = {ndx / cp[0], ndy / cp[1], -1.0f};
+    float e1[3], e2[3], tv[3], pv[3], qv[3];
+    for (int k = 0; k < 3; ++k) { e1[k] = v[1][k] - v[0][k]; e2[k] = v[2][k] - v[0][k]; tv[k] = -v[0][k]; }
+    cross3(r, e2, pv);
+    float det = dot3(e1, pv);
+    float u = dot3(tv, pv) / det;
+    cross3(tv, e1, qv);
+    float w = dot3(r, qv) / det;
+    float b0 = 1.0f - u;
+    b0 = b0 - w;
+    b[0] = b0; b[1] = u; b[2] = w;
+}
+
 /* Section 4.4: pixel -> (instance, triangle) by binary search of the prefix
  * sum, then the barycentrics of the pixel-centre ray with the triangle in
  * view space (camera at the origin; Moeller-Trumbore form, unclamped).
@@ -476,19 +502,7 @@ static int pixel_bary(const orc_mesh *meshes, const orc_instance *inst, int n_in
         vidx[k] = m->idx[3 * t + (uint64_t)k];
         view_space(mv, m->pos + 3 * (uint64_t)vidx[k], v[k]);
     }
-    float ndx = ((float)(2 * x + 1) / (float)cam->W) - 1.0f;
-    float ndy = ((float)(2 * y + 1) / (float)cam->H) - 1.0f;
-    float r[3] = {ndx / cp[0], ndy / cp[1], -1.0f};
-    float e1[3], e2[3], tv[3], pv[3], qv[3];
-    for (int k = 0; k < 3; ++k) { e1[k] = v[1][k] - v[0][k]; e2[k] = v[2][k] - v[0][k]; tv[k] = -v[0][k]; }
-    cross3(r, e2, pv);
-    float det = dot3(e1, pv);
-    float u = dot3(tv, pv) / det;
-    cross3(tv, e1, qv);
-    float w = dot3(r, qv) / det;
-    float b0 = 1.0f - u;
-    b0 = b0 - w;
-    b[0] = b0; b[1] = u; b[2] = w;
+    ray_bary(v, cam, cp, x, y, b);
     *mesh_out = m;
     return 1;
 }
@@ -500,6 +514,20 @@ static float interp3(const float b[3], float c0, float c1, float c2)
     float s = p + q;
     float r = b[2] * c2;
     return s + r;
+}
+
+/* One resolved pixel: FP32 RGBA, and RGBA8 = rint(clamp(c, 0, 1) * 255). */
+static void put_pixel(const float out[4], size_t pix, float *rgba, uint8_t *rgba8)
+{
+    for (int ch = 0; ch < 4; ++ch) {
+        if (rgba) rgba[4 * pix + ch] = out[ch];
+        if (rgba8) {
+            float c = out[ch];
+            if (!(c >= 0.0f)) c = 0.0f;
+            if (c > 1.0f) c = 1.0f;
+            rgba8[4 * pix + ch] = (uint8_t)rintf(c * 255.0f);
+        }
+    }
 }
 
 /* Resolve with the meshes' RGBA8 vertex colours (c = byte / 255): FP32 RGBA
@@ -526,15 +554,123 @@ int orc_resolve(const orc_mesh *meshes, int n_meshes, const orc_instance *inst, 
                     out[ch] = interp3(b, c0, c1, c2);
                 }
             }
-            for (int ch = 0; ch < 4; ++ch) {
-                if (rgba) rgba[4 * pix + ch] = out[ch];
-                if (rgba8) {
-                    float c = out[ch];
-                    if (!(c >= 0.0f)) c = 0.0f;
-                    if (c > 1.0f) c = 1.0f;
-                    rgba8[4 * pix + ch] = (uint8_t)rintf(c * 255.0f);
+            put_pixel(out, pix, rgba, rgba8);
+        }
+    free(base);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------- textured resolve (R17) */
+
+/* A mesh's texture: per-vertex texture coordinates and a square RGBA8 mip
+ * chain of side 2^log2_size: level l (0 .. log2_size) holds (2^(log2_size-l))^2
+ * texels, row-major with row 0 at v = 0, and the levels follow one another. */
+typedef struct {
+    const float *uv;        /* V x 2, or NULL: the mesh has no texture */
+    const uint8_t *texels;
+    int32_t log2_size;
+    int32_t pad;
+} orc_texture;
+
+/* floor(log2(F)) for a finite F >= 1, read off the exponent of the float. */
+static int floor_log2f(float F)
+{
+    int e;
+    frexpf(F, &e);         /* F = m 2^e with m in [0.5, 1) */
+    return e - 1;
+}
+
+/* Section 4.4 "Shading and Mip Mapping": the mip level of a pixel comes from
+ * the pixel footprint in texture space.  Rays through the centres of the
+ * pixel and of its right (x + 1), top (y + 1) and top-right neighbours meet
+ * the plane of the pixel's triangle; their barycentrics (unclamped, so
+ * points off the triangle extrapolate) interpolate the vertex texture
+ * coordinates; the footprint is the larger side of the four samples' uv
+ * bounding box in level-0 texels, F = max(du, dv) 2^log2_size, and the level
+ * is floor(log2(F)), clamped to 0 .. log2_size (0 when F < 1).  The colour is
+ * the nearest texel of that level at the pixel's own uv -- column
+ * floor(u s), row floor(v s) with s the level's side, clamped to the level --
+ * as c = byte / 255; RGBA8 as in orc_resolve.  Pixels of meshes without a
+ * texture take orc_resolve's vertex colours.  level: W*H bytes or NULL, the
+ * chosen level, 255 for background and untextured pixels. */
+int orc_resolve_textured(const orc_mesh *meshes, int n_meshes, const orc_texture *tex,
+                         const orc_instance *inst, int n_inst, const orc_camera *cam, const uint64_t *vis,
+                         float *rgba, uint8_t *rgba8, uint8_t *level)
+{
+    float cp[3];
+    if (orc_camera_params(cam->proj, cp) != ORC_OK) return ORC_BAD_CAMERA;
+    uint64_t *base = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)n_inst + 1));
+    int st = orc_bases(meshes, n_meshes, inst, n_inst, base);
+    if (st != ORC_OK) { free(base); return st; }
+    for (int y = 0; y < cam->H; ++y)
+        for (int x = 0; x < cam->W; ++x) {
+            size_t pix = (size_t)y * (size_t)cam->W + (size_t)x;
+            float out[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            int lev = 255;
+            uint64_t key = vis[pix];
+            if (key != ORC_EMPTY) {
+                uint64_t id = key & ORC_ID_MASK;
+                int i = (int)upper_bound_u64(base, n_inst, id) - 1;
+                uint64_t t = id - base[i];
+                const orc_mesh *m = &meshes[inst[i].mesh];
+                const orc_texture *tx = &tex[inst[i].mesh];
+                float mv[12], v[3][3];
+                uint32_t vi[3];
+                orc_model_view(cam->view, inst[i].model, mv);
+                for (int k = 0; k < 3; ++k) {
+                    vi[k] = m->idx[3 * t + (uint64_t)k];
+                    view_space(mv, m->pos + 3 * (uint64_t)vi[k], v[k]);
+                }
+                if (tx->uv) {
+                    /* the four samples: (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) */
+                    float us[4], vs[4];
+                    for (int q = 0; q < 4; ++q) {
+                        float b[3];
+                        ray_bary(v, cam, cp, x + (q & 1), y + (q >> 1), b);
+                        us[q] = interp3(b, tx->uv[2 * (uint64_t)vi[0]], tx->uv[2 * (uint64_t)vi[1]],
+                                        tx->uv[2 * (uint64_t)vi[2]]);
+                        vs[q] = interp3(b, tx->uv[2 * (uint64_t)vi[0] + 1], tx->uv[2 * (uint64_t)vi[1] + 1],
+                                        tx->uv[2 * (uint64_t)vi[2] + 1]);
+                    }
+                    float umin = fminf(fminf(us[0], us[1]), fminf(us[2], us[3]));
+                    float umax = fmaxf(fmaxf(us[0], us[1]), fmaxf(us[2], us[3]));
+                    float vmin = fminf(fminf(vs[0], vs[1]), fminf(vs[2], vs[3]));
+                    float vmax = fmaxf(fmaxf(vs[0], vs[1]), fmaxf(vs[2], vs[3]));
+                    float du = umax - umin;
+                    float dv = vmax - vmin;
+                    float F = fmaxf(du, dv) * (float)(1 << tx->log2_size);
+                    lev = 0;
+                    if (F >= 1.0f) lev = isfinite(F) ? floor_log2f(F) : tx->log2_size;
+                    if (lev > tx->log2_size) lev = tx->log2_size;
+                    /* level lev starts after the (4^L - 4^(L - lev)) / 3 texels of the finer levels */
+                    int side = 1 << (tx->log2_size - lev);
+                    uint64_t off = 0;
+                    for (int l = 0; l < lev; ++l) {
+                        uint64_t sl = (uint64_t)1 << (tx->log2_size - l);
+                        off += sl * sl;
+                    }
+                    float fs = (float)side;
+                    float cu = floorf(us[0] * fs);
+                    float cv = floorf(vs[0] * fs);
+                    if (!(cu >= 0.0f)) cu = 0.0f;
+                    if (cu > fs - 1.0f) cu = fs - 1.0f;
+                    if (!(cv >= 0.0f)) cv = 0.0f;
+                    if (cv > fs - 1.0f) cv = fs - 1.0f;
+                    uint64_t texel = off + (uint64_t)cv * (uint64_t)side + (uint64_t)cu;
+                    for (int ch = 0; ch < 4; ++ch) out[ch] = (float)tx->texels[4 * texel + (uint64_t)ch] / 255.0f;
+                } else if (m->rgba8) {
+                    float b[3];
+                    ray_bary(v, cam, cp, x, y, b);
+                    for (int ch = 0; ch < 4; ++ch) {
+                        float c0 = (float)m->rgba8[4 * (uint64_t)vi[0] + ch] / 255.0f;
+                        float c1 = (float)m->rgba8[4 * (uint64_t)vi[1] + ch] / 255.0f;
+                        float c2 = (float)m->rgba8[4 * (uint64_t)vi[2] + ch] / 255.0f;
+                        out[ch] = interp3(b, c0, c1, c2);
+                    }
                 }
             }
+            if (level) level[pix] = (uint8_t)lev;
+            put_pixel(out, pix, rgba, rgba8);
         }
     free(base);
     return ORC_OK;

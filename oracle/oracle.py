@@ -47,6 +47,10 @@ class _Mesh(C.Structure):
                 ("rgba8", C.c_void_p)]
 
 
+class _Texture(C.Structure):
+    _fields_ = [("uv", C.c_void_p), ("texels", C.c_void_p), ("log2_size", C.c_int32), ("pad", C.c_int32)]
+
+
 class _Instance(C.Structure):
     _fields_ = [("mesh", C.c_uint32), ("pad", C.c_uint32), ("model", C.c_float * 16)]
 
@@ -68,6 +72,9 @@ def _lib():
                                            C.POINTER(_Camera), C.c_uint32, C.c_uint32, C.c_void_p]
             L.orc_resolve.argtypes = [C.POINTER(_Mesh), C.c_int, C.POINTER(_Instance), C.c_int,
                                       C.POINTER(_Camera), C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_resolve_textured.argtypes = [C.POINTER(_Mesh), C.c_int, C.POINTER(_Texture), C.POINTER(_Instance),
+                                               C.c_int, C.POINTER(_Camera), C.c_void_p, C.c_void_p, C.c_void_p,
+                                               C.c_void_p]
             L.orc_interpolate.argtypes = [C.POINTER(_Mesh), C.c_int, C.POINTER(_Instance), C.c_int,
                                           C.POINTER(_Camera), C.c_void_p, C.c_uint32, C.c_void_p, C.c_int,
                                           C.c_void_p, C.c_void_p]
@@ -186,6 +193,33 @@ def resolve(osc: OracleScene, camera, vis: np.ndarray):
     if st != 0:
         raise ValueError(f"orc_resolve failed: {st}")
     return rgba, rgba8
+
+
+def resolve_textured(osc: OracleScene, camera, vis: np.ndarray, textures):
+    """Resolve with textures and the 4-ray mip-level choice (Section 4.4).
+    textures: one entry per mesh, None or (uv (V, 2) float32, flat RGBA8 mip
+    chain, log2_size).  Returns (rgba float32 (H, W, 4), rgba8, level uint8
+    (H, W), 255 where no texture was sampled)."""
+    vis = np.ascontiguousarray(vis, np.uint64)
+    tx = (_Texture * osc.n_meshes)()
+    keep = []
+    for k, t in enumerate(textures):
+        if t is None:
+            continue
+        uv = _np(t[0], np.float32)
+        tex = _np(t[1], np.uint8)
+        keep += [uv, tex]
+        tx[k].uv = uv.ctypes.data
+        tx[k].texels = tex.ctypes.data
+        tx[k].log2_size = int(t[2])
+    rgba = np.zeros((camera.H, camera.W, 4), np.float32)
+    rgba8 = np.zeros((camera.H, camera.W, 4), np.uint8)
+    level = np.zeros((camera.H, camera.W), np.uint8)
+    st = _lib().orc_resolve_textured(osc.meshes, osc.n_meshes, tx, osc.inst, osc.n_inst, C.byref(_cam(camera)),
+                                     vis.ctypes.data, rgba.ctypes.data, rgba8.ctypes.data, level.ctypes.data)
+    if st != 0:
+        raise ValueError(f"orc_resolve_textured failed: {st}")
+    return rgba, rgba8, level
 
 
 # ------------------------------------------------------------ compression --

@@ -170,6 +170,41 @@ def heightfield_mesh(n: int, seed: int, device="cpu", amplitude: float = 0.2,
     return Mesh(pos=pos, idx=idx, rgba8=rgba, aabb=aabb)
 
 
+def grid_uv(n: int, device="cpu") -> torch.Tensor:
+    """Texture coordinates of a heightfield of n x n cells: vertex (i, j)
+    (index j (n + 1) + i) gets (u, v) = (i / n, j / n), its x and z in the
+    unit square, as (V, 2) float32."""
+    k = torch.arange(n + 1, device=device, dtype=torch.float64) / float(n)
+    v = k[:, None].expand(n + 1, n + 1).reshape(-1)
+    u = k[None, :].expand(n + 1, n + 1).reshape(-1)
+    return torch.stack([u, v], dim=1).to(torch.float32)
+
+
+def texture_mip_chain(log2_size: int, seed: int, device="cpu") -> torch.Tensor:
+    """A seeded square RGBA8 texture of side 2^log2_size with its full mip
+    chain, flat: level l (side 2^(log2_size - l)) follows level l - 1, each
+    row-major with row 0 at v = 0.  Level 0 holds hashed random RGB bytes
+    (alpha 255) on 8 x 8 texel blocks modulated by a per-texel hash, so that
+    every level differs; each coarser level is the 2 x 2 box average of the
+    one before, (a + b + c + d + 2) >> 2 per channel."""
+    side = 1 << log2_size
+    j = torch.arange(side, device=device, dtype=torch.int64)
+    jj, ii = j[:, None].expand(side, side), j[None, :].expand(side, side)
+    blk = (jj >> 3) * 65536 + (ii >> 3)
+    tex = []
+    for ch, salt in enumerate((11, 23, 37)):
+        coarse = _hash32(blk * 7 + salt + seed * 131) & 0xFF
+        fine = _hash32((jj * side + ii) * 5 + salt * 3 + seed) & 0x3F
+        tex.append(((coarse * 3 + fine * 4) >> 2).clamp(0, 255))
+    tex.append(torch.full_like(tex[0], 255))
+    lev = torch.stack(tex, dim=2)                      # (side, side, 4) int64
+    out = [lev.reshape(-1)]
+    while lev.shape[0] > 1:
+        lev = (lev[0::2, 0::2] + lev[0::2, 1::2] + lev[1::2, 0::2] + lev[1::2, 1::2] + 2) >> 2
+        out.append(lev.reshape(-1))
+    return torch.cat(out).to(torch.uint8)
+
+
 def sphere_mesh(n: int, seed: int, device="cpu", amplitude: float = 0.2) -> Mesh:
     """UV sphere of n latitude x 2n longitude cells with radius 1 + noise.
 

@@ -49,8 +49,8 @@ C_MUTATIONS = [
      "float ndx = ((float)(2 * x) / (float)cam->W) - 1.0f;"),
     ("interpolation, wrong colour index", "    float q = b[1] * c1;", "    float q = b[1] * c2;"),
     ("resolve, upper clamp of RGBA8 dropped",
-     "                    float c = out[ch];\n                    if (!(c >= 0.0f)) c = 0.0f;\n                    if (c > 1.0f) c = 1.0f;",
-     "                    float c = out[ch];\n                    if (!(c >= 0.0f)) c = 0.0f;"),
+     "            float c = out[ch];\n            if (!(c >= 0.0f)) c = 0.0f;\n            if (c > 1.0f) c = 1.0f;",
+     "            float c = out[ch];\n            if (!(c >= 0.0f)) c = 0.0f;"),
     ("box filter, divides by ss", "    const float n = (float)(ss * ss);", "    const float n = (float)(ss);"),
     ("box filter, wrong sample row", "size_t f = (size_t)(ss * y + sy) * (size_t)Wf", "size_t f = (size_t)(ss * y + sx) * (size_t)Wf"),
     ("index bits, log2 of the span", "((uint64_t)1 << b) < (uint64_t)span + 1", "((uint64_t)1 << b) < (uint64_t)span"),
@@ -64,6 +64,19 @@ C_MUTATIONS = [
     ("ray cast, b0 from u twice", "            b0 = b0 - w;\n            float t", "            b0 = b0 - u;\n            float t"),
     ("ray cast, depth from e1", "float t = dot3(e2, qv) / det;", "float t = dot3(e1, qv) / det;"),
     ("ray cast routing, s2 threshold", "> (int64_t)s2_max) {", ">= (int64_t)s2_max) {"),
+    ("mip rays, left neighbour", "ray_bary(v, cam, cp, x + (q & 1), y + (q >> 1), b);",
+     "ray_bary(v, cam, cp, x - (q & 1), y + (q >> 1), b);"),
+    ("mip rays, no top neighbour", "ray_bary(v, cam, cp, x + (q & 1), y + (q >> 1), b);",
+     "ray_bary(v, cam, cp, x + (q & 1), y, b);"),
+    ("mip level rounded", "lev = isfinite(F) ? floor_log2f(F) : tx->log2_size;",
+     "lev = isfinite(F) ? (int)rintf(log2f(F)) : tx->log2_size;"),
+    ("mip footprint from u only", "float F = fmaxf(du, dv) * (float)(1 << tx->log2_size);",
+     "float F = du * (float)(1 << tx->log2_size);"),
+    ("texel row and column swapped", "uint64_t texel = off + (uint64_t)cv * (uint64_t)side + (uint64_t)cu;",
+     "uint64_t texel = off + (uint64_t)cu * (uint64_t)side + (uint64_t)cv;"),
+    ("mip level offset", "        off += sl * sl;\n", "        off += sl;\n"),
+    ("texture v from u", "tx->uv[2 * (uint64_t)vi[1] + 1]", "tx->uv[2 * (uint64_t)vi[1]]"),
+    ("texel from the right neighbour's uv", "float cu = floorf(us[0] * fs);", "float cu = floorf(us[1] * fs);"),
     ("clip, near-plane w interpolated", "    if (p == 0) r.w = nearv;\n    else if (r.w < nearv) r.w = nearv;",
      "    if (r.w < nearv) r.w = nearv;"),
     ("ray cast routing, extent rule dropped", "int large = mxx - mnx >= 16384 || mxy - mny >= 16384 ||",

@@ -868,3 +868,144 @@ def test_snap_ties_round_to_even(oracle_lib):
         assert inside.all()
         np.testing.assert_array_equal(XY[:, 0], np.rint(k + frac))          # numpy rint: half to even
         np.testing.assert_array_equal(XY[:, 1], np.rint(k[::-1] + frac))
+
+
+# ------------------------------------------------- textured resolve (R17) ---
+def _coord_texture(L):
+    """Mip chain of side 2^L (L <= 8) whose texel (column c, row r) of level l
+    holds (c, r, l, 255): the resolved RGBA8 names the texel that was read."""
+    out = []
+    for l in range(L + 1):
+        s = 1 << (L - l)
+        r, c = np.meshgrid(np.arange(s), np.arange(s), indexing="ij")
+        out.append(np.stack([c, r, np.full_like(c, l), np.full_like(c, 255)], axis=2).reshape(-1))
+    return np.concatenate(out).astype(np.uint8)
+
+
+def _plane_quad(a, b, D, u_span, v_span):
+    """Camera-facing rectangle |x| <= a, |y| <= b at view depth D (camera at
+    the origin looking down -z), front face towards the camera, texture
+    coordinates u = (x + a) / (2a) * u_span, v = (y + b) / (2b) * v_span."""
+    pos = np.array([[-a, -b, -D], [a, -b, -D], [-a, b, -D], [a, b, -D]], np.float64)
+    uv = np.stack([(pos[:, 0] + a) / (2 * a) * u_span, (pos[:, 1] + b) / (2 * b) * v_span], 1)
+    return pos, [[0, 1, 2], [2, 1, 3]], uv.astype(np.float32)
+
+
+def test_mip_level_of_a_camera_facing_plane(oracle_lib):
+    """Section 4.4: the four rays through the pixel and its right, top and
+    top-right neighbours meet a camera-facing plane at D / (W fx) and
+    D / (H fy) apart; with the texture repeated `span` times over the 2a x 2b
+    rectangle the footprint is F = 2^L span max(D / (W fx a), D / (H fy b))
+    level-0 texels, the same for every pixel, and the level is floor(log2 F)
+    clamped to 0..L.  Depth and span are chosen with log2 F 0.6 above an
+    integer (round would pick the next level), plus one case below a texel
+    per pixel (level 0) and one beyond the coarsest level (clamped).  The sampled texel is the float64 floor(u s), floor(v s)
+    of the pixel's own uv, s the level's side, away from texel boundaries."""
+    O = oracle_lib
+    W, H, L = 64, 48, 8
+    proj = S.perspective(60.0, W / H, 0.01, 1000.0)
+    cp = O.camera_params(proj.astype(np.float32)).astype(np.float64)
+    fx, fy = cp[0], cp[1]
+    a, b = 1.5, 0.5
+    tex = _coord_texture(L)
+    seen = set()
+    c = 2 ** L * max(1 / (W * fx * a), 1 / (H * fy * b))     # F = c D span
+    targets = [0.3] + [2 ** (k + 0.6) for k in range(L)] + [2 ** (L + 1.5)]
+    for k, Ft in enumerate(targets):
+        D = 0.8 * (1 + k % 3)
+        span = Ft / (c * D)
+        F = c * D * span
+        want = 0 if F < 1 else min(int(math.floor(math.log2(F))), L)
+        pos, idx, uv = _plane_quad(a, b, D, span, span)
+        sc = Scene([mesh_np(pos, idx)], [Instance(0, ident())])
+        cam = _cam(np.eye(4), proj, W, H)
+        osc = O.OracleScene(sc)
+        vis = O.render(osc, cam)
+        cov = vis != O.EMPTY
+        assert cov.sum() >= 1
+        _, rgba8, lev = O.resolve_textured(osc, cam, vis, [(uv, tex, L)])
+        assert (lev[cov] == want).all(), (D, want, np.unique(lev[cov]))
+        assert (lev[~cov] == 255).all()
+        seen.add(want)
+        # the texel of the pixel's own uv, from a float64 ray-plane hit
+        ys, xs = np.nonzero(cov)
+        ndx, ndy = (2 * xs + 1) / W - 1, (2 * ys + 1) / H - 1
+        px, py = D * ndx / fx, D * ndy / fy
+        u, v = (px + a) / (2 * a) * span, (py + b) / (2 * b) * span
+        side = 1 << (L - want)
+        cu, cv = u * side, v * side
+        clear = (np.abs(cu - np.round(cu)) > 1e-3) & (np.abs(cv - np.round(cv)) > 1e-3)
+        got = rgba8[ys, xs]
+        assert clear.sum() > 0.5 * len(xs)
+        np.testing.assert_array_equal(got[clear, 0], np.clip(np.floor(cu[clear]), 0, side - 1))
+        np.testing.assert_array_equal(got[clear, 1], np.clip(np.floor(cv[clear]), 0, side - 1))
+        assert (got[:, 2] == want).all()
+    assert seen == set(range(L + 1))
+
+
+def test_mip_level_of_a_tilted_plane_matches_float64(oracle_lib):
+    """A plane seen at a grazing angle (the footprint grows quickly towards
+    the horizon and differs along x and y): per pixel, the four float64
+    ray-plane hits give the uv samples, their bounding box the footprint and
+    floor(log2 F) the level; the oracle's level must agree wherever log2 F
+    is at least 1e-3 from an integer, and its texel wherever u s and v s are
+    at least 1e-3 from a texel edge."""
+    O = oracle_lib
+    W, H, L = 96, 64, 8
+    tex = _coord_texture(L)
+    view = S.look_at((0.3, 0.35, 2.2), (0.55, 0.0, -0.4))
+    proj = S.perspective(70.0, W / H, 0.01, 100.0)
+    cam = _cam(view, proj, W, H)
+    pos = np.array([[-2.0, 0.0, 3.0], [3.0, 0.0, 3.0], [-2.0, 0.0, -6.0], [3.0, 0.0, -6.0]])
+    idx = [[0, 1, 2], [2, 1, 3]]
+    # u along x over 5 units, v along -z over 9 units, rotated texture: u and v each mix x and z
+    uvm = np.array([[0.15, -0.05], [0.02, 0.09]])
+    uv = ((pos[:, [0, 2]] - [-2.0, 3.0]) @ uvm.T).astype(np.float32)
+    sc = Scene([mesh_np(pos, idx)], [Instance(0, ident())])
+    osc = O.OracleScene(sc)
+    vis = O.render(osc, cam)
+    cov = vis != O.EMPTY
+    _, rgba8, lev = O.resolve_textured(osc, cam, vis, [(uv, tex, L)])
+    cp = O.camera_params(np.asarray(proj, np.float32)).astype(np.float64)
+    V = np.asarray(view, np.float64)
+    Vi = np.linalg.inv(V)
+    eye = Vi[:3, 3]
+    ys, xs = np.nonzero(cov)
+
+    def hit_uv(x, y):
+        ndx, ndy = (2 * x + 1) / W - 1, (2 * y + 1) / H - 1
+        d = Vi[:3, :3] @ np.stack([ndx / cp[0], ndy / cp[1], -np.ones_like(ndx)])
+        t = -eye[1] / d[1]
+        p = eye[:, None] + d * t
+        return uvm @ (p[[0, 2]] - np.array([[-2.0], [3.0]]))
+
+    s = [hit_uv(xs + (q & 1), ys + (q >> 1)) for q in range(4)]
+    us, vs = np.stack([q[0] for q in s]), np.stack([q[1] for q in s])
+    F = np.maximum(us.max(0) - us.min(0), vs.max(0) - vs.min(0)) * 2 ** L
+    lg = np.log2(F)
+    want = np.where(F < 1, 0, np.minimum(np.floor(lg), L)).astype(int)
+    clear = np.abs(lg - np.round(lg)) > 1e-3
+    assert clear.mean() > 0.95 and len(np.unique(want)) >= 4
+    np.testing.assert_array_equal(lev[ys, xs][clear], want[clear])
+    side = (1 << (L - lev[ys, xs].astype(int))).astype(np.float64)
+    cu, cv = s[0][0] * side, s[0][1] * side
+    ok = clear & (np.abs(cu - np.round(cu)) > 1e-3) & (np.abs(cv - np.round(cv)) > 1e-3)
+    assert ok.mean() > 0.9
+    got = rgba8[ys, xs].astype(int)
+    np.testing.assert_array_equal(got[ok, 0], np.clip(np.floor(cu[ok]), 0, side[ok] - 1))
+    np.testing.assert_array_equal(got[ok, 1], np.clip(np.floor(cv[ok]), 0, side[ok] - 1))
+
+
+def test_textured_resolve_without_textures_is_the_plain_resolve(oracle_lib):
+    """Meshes without a texture keep the vertex colours of the plain resolve
+    (Section 4.4), and report no level."""
+    O = oracle_lib
+    sc = S.scene_small(n=32, W=80, H=60)
+    cam = sc.cameras[0]
+    osc = O.OracleScene(sc)
+    vis = O.render(osc, cam)
+    f, e8 = O.resolve(osc, cam, vis)
+    g, g8, lev = O.resolve_textured(osc, cam, vis, [None] * len(sc.meshes))
+    np.testing.assert_array_equal(g, f)
+    np.testing.assert_array_equal(g8, e8)
+    assert (lev == 255).all()
