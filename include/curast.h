@@ -106,6 +106,18 @@ typedef struct {
                                     off-screen triangles itself (the result is the same;
                                     for measuring what the conservative cull saves);
                                     0 (default)                                              */
+    uint32_t stage1_vertex_reuse; /* 1: single-pair items of uncompressed meshes stage the
+                                    vertex ranges their indices reference in shared memory
+                                    and transform each vertex once (Section 6, vertex
+                                    reuse); 0 (default): every triangle gathers and
+                                    transforms its three vertices, which runs faster on
+                                    GB300 (the result is the same)                           */
+    uint32_t stage3_tile_buffer; /* 1 (default): stage 3 sorts its tile parts by tile and
+                                    gives each tile a shared-memory framebuffer (Section
+                                    4.3): the parts of a tile meet there, and each covered
+                                    pixel takes one global atomic minimum; 0: every covered
+                                    pixel of every part goes to the global buffer (the
+                                    result is the same)                                     */
     uint32_t reserved;           /* 0                                                        */
 } curast_config;
 

@@ -49,7 +49,8 @@ class Config(C.Structure):
                 ("queue1_capacity", C.c_uint64), ("queue2_capacity", C.c_uint64), ("check_indices", C.c_uint32),
                 ("collect_stats", C.c_uint32), ("stage1_bitmap_bytes", C.c_uint64),
                 ("stage1_group_min_pairs", C.c_uint32), ("stage3_raycast", C.c_uint32),
-                ("stage1_exact_all", C.c_uint32), ("reserved", C.c_uint32)]
+                ("stage1_exact_all", C.c_uint32), ("stage1_vertex_reuse", C.c_uint32),
+                ("stage3_tile_buffer", C.c_uint32), ("reserved", C.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 SOURCES = ["raster.cu", "shade.cu", "runtime.cu", "static_render.cu", "compress.cu"]
-HEADERS = ["device.cuh", "internal.h", "stage1.cuh"]
+HEADERS = ["device.cuh", "internal.h", "stage1.cuh", "stage1_win.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

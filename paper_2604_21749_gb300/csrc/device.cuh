@@ -24,6 +24,8 @@ struct ViewDev {             // one view of a frame
     float fx, fy, nearv;     // projection vector (Eq. 2) and near plane
     float hw, hh;            // W/2, H/2
     int32_t W, H;
+    uint32_t tile0;          // stage-3 tiles: index of this view's first tile in the frame
+    uint32_t ntx;            // tiles per row (ceil(W / tile side))
     uint64_t *vis;           // W*H visibility words
 };
 
@@ -123,6 +125,8 @@ struct Counters {
     unsigned long long overflow1, overflow2;
     unsigned int error, pad;
     unsigned long long stats[8];      // see Stat
+    unsigned long long s3_next;       // binned stage 3: tiles taken
+    unsigned long long s3_tiles;      // binned stage 3: tiles with at least one part
 };
 
 enum Stat { kStatIn = 0, kStatClip, kStatBack, kStatTiny, kStatS1, kStatS2, kStatParts, kStatFast, kStatCount };
@@ -158,6 +162,14 @@ struct FrameDev {
     uint32_t stats;          // count statistics
     uint32_t group_min;      // instanced items with >= this many pairs (> 0) run the group test
     uint32_t s3_ray;         // 1: triangles past s2_max take the paper's ray-cast stage 3
+    // binned stage 3 (s3_bin = 1): queue-2 parts sorted by tile, one block per tile
+    uint32_t s3_bin;
+    uint32_t n_tiles;        // tiles of all views
+    uint32_t *tile_cnt;      // n_tiles: parts per tile (counted by stage 2)
+    uint32_t *tile_start;    // n_tiles + 1: exclusive prefix sum of tile_cnt
+    uint32_t *tile_fill;     // n_tiles: scatter cursors
+    uint32_t *tile_list;     // tiles with at least one part
+    uint32_t *part_sorted;   // q2_cap: queue-2 indices in tile order
 };
 
 constexpr unsigned kErrIndex = 1u;     // a vertex index >= V was skipped
@@ -338,6 +350,19 @@ __device__ __forceinline__ void shade_pixel(const SubTri &s, int x, int y, uint6
     depth_test_write(vis, (size_t)y * (size_t)W + (size_t)x, frag_key(E0, E1, E2, s.A, s.iz, s.id));
 }
 
+// The coverage test and word of shade_pixel without the write: false when the
+// pixel centre is not covered.
+__device__ __forceinline__ bool pixel_key(const SubTri &s, int x, int y, uint64_t &key) {
+    const int64_t px = 256 * (int64_t)x + 128, py = 256 * (int64_t)y + 128;
+    const int64_t E0 = (int64_t)(s.X[2] - s.X[1]) * (py - s.Y[1]) - (int64_t)(s.Y[2] - s.Y[1]) * (px - s.X[1]);
+    const int64_t E1 = (int64_t)(s.X[0] - s.X[2]) * (py - s.Y[2]) - (int64_t)(s.Y[0] - s.Y[2]) * (px - s.X[2]);
+    const int64_t E2 = (int64_t)(s.X[1] - s.X[0]) * (py - s.Y[0]) - (int64_t)(s.Y[1] - s.Y[0]) * (px - s.X[0]);
+    const int64_t b0 = s.bias & 1u, b1 = (s.bias >> 1) & 1u, b2 = (s.bias >> 2) & 1u;
+    if (((E0 - b0) | (E1 - b1) | (E2 - b2)) < 0) return false;
+    key = frag_key(E0, E1, E2, s.A, s.iz, s.id);
+    return true;
+}
+
 // Pixels i = start, start + stride, ... of the sub-triangle's pixel range
 // (x = x0 + i mod w, y = y0 + i / w: the 1D loop of Section 4.2), optionally
 // restricted to a sub-rectangle.
@@ -409,18 +434,23 @@ __device__ __forceinline__ RayTri ray_setup(float3 v0, float3 v1, float3 v2) {
     return R;
 }
 
-__device__ __forceinline__ void ray_pixel(const RayTri &R, int x, int y, const ViewDev &vw, uint64_t id) {
+__device__ __forceinline__ bool ray_key(const RayTri &R, int x, int y, const ViewDev &vw, uint64_t id, uint64_t &key) {
     const float3 r = pixel_ray(x, y, vw.W, vw.H, vw.fx, vw.fy);
     const float3 pv = cross3(r, R.e2);
     const float det = dot3(R.e1, pv);
-    if (!(det > 0.0f)) return;
+    if (!(det > 0.0f)) return false;
     const float u = __fdiv_rn(dot3(R.tv, pv), det);
     const float w = __fdiv_rn(dot3(r, R.qv), det);
     const float b0 = __fsub_rn(__fsub_rn(1.0f, u), w);
     const float t = __fdiv_rn(dot3(R.e2, R.qv), det);
-    if (!(u >= 0.0f && w >= 0.0f && b0 >= 0.0f && t >= vw.nearv)) return;
-    const uint64_t key = ((uint64_t)(__float_as_uint(t) >> 3) << 36) | (id & kIdMask);
-    depth_test_write(vw.vis, (size_t)y * (size_t)vw.W + (size_t)x, key);
+    if (!(u >= 0.0f && w >= 0.0f && b0 >= 0.0f && t >= vw.nearv)) return false;
+    key = ((uint64_t)(__float_as_uint(t) >> 3) << 36) | (id & kIdMask);
+    return true;
+}
+
+__device__ __forceinline__ void ray_pixel(const RayTri &R, int x, int y, const ViewDev &vw, uint64_t id) {
+    uint64_t key;
+    if (ray_key(R, x, y, vw, id, key)) depth_test_write(vw.vis, (size_t)y * (size_t)vw.W + (size_t)x, key);
 }
 
 // Pixels i = start, start + stride, ... of [x0, x1] x [y0, y1] by ray cast.

@@ -7,10 +7,12 @@
 namespace curast {
 
 struct LaunchShape {
-    int stage1_blocks_per_sm[2][3];   // [instanced][variant: 0 cull, 1 fused, 2 cull of compressed meshes]
+    int stage1_blocks_per_sm[2][4];   // [instanced][variant: 0 cull, 1 fused, 2 cull of compressed meshes,
+                                      //  3 single-pair cull with vertex windows (not instanced)]
     int stage1x_blocks_per_sm;        // exact kernel of stage 1
     int stage2_blocks_per_sm;
     int stage3_blocks_per_sm;
+    int stage3t_blocks_per_sm[4];     // binned stage 3 per tile side 2^4 .. 2^7
     int num_sms;
 };
 
@@ -23,6 +25,9 @@ cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32
 cudaError_t launch_stage1_exact(const FrameDev &f, uint32_t r, int blocks, cudaStream_t s);
 cudaError_t launch_stage2(const FrameDev &f, int blocks, cudaStream_t s);
 cudaError_t launch_stage3(const FrameDev &f, int blocks, cudaStream_t s);
+// Binned stage 3: scan of the per-tile part counts, scatter of the parts into
+// tile order, then one block per tile with the tile's words in shared memory.
+cudaError_t launch_stage3_binned(const FrameDev &f, int scatter_blocks, int tile_blocks, cudaStream_t s);
 // scratch: 256 * 6 floats; out6: xmin ymin zmin xmax ymax zmax
 cudaError_t launch_aabb(const float *pos, uint64_t V, float *scratch, float *out6, cudaStream_t s);
 // Section 4.6 encoding (compress.cu)

@@ -248,6 +248,7 @@ __device__ __forceinline__ int classify(const FrameDev &f, const Rec r[3], const
 }
 
 #include "stage1.cuh"
+#include "stage1_win.cuh"
 
 // ---------------------------------------------------------------- stage 2 --
 // Section 4.2: one warp per queued triangle.  The triangle is clipped
@@ -277,6 +278,7 @@ __device__ __forceinline__ void q2_append(const FrameDev &f, bool want, const Su
         e.pair = 0;
         e.ray = 0;
         f.q2[slot] = e;
+        if (f.s3_bin) atomicAdd(&f.tile_cnt[vw.tile0 + (uint32_t)ty * vw.ntx + (uint32_t)tx], 1u);
     } else {
         atomicAdd(&f.ctr->overflow2, 1ull);
         const int ts = 1 << f.tile_log2;
@@ -311,6 +313,7 @@ __device__ __forceinline__ void q2_append_ray(const FrameDev &f, bool want, uint
         e.pair = pidx;
         e.ray = 1;
         f.q2[slot] = e;
+        if (f.s3_bin) atomicAdd(&f.tile_cnt[vw.tile0 + (uint32_t)ty * vw.ntx + (uint32_t)tx], 1u);
     } else {
         atomicAdd(&f.ctr->overflow2, 1ull);
         const int ts = 1 << f.tile_log2;
@@ -434,6 +437,167 @@ __global__ void __launch_bounds__(256) k_stage3(FrameDev f) {
     }
 }
 
+// ------------------------------------------------------- binned stage 3 --
+// Section 4.3 with the tile framebuffer in shared memory: the parts stage 2
+// queued are sorted by tile (stage 2 counts them per tile; one block scans
+// the counts; a scatter pass writes the part indices in tile order), then one
+// block takes one tile at a time, keeps the tile's words in shared memory,
+// applies every part of the tile there with a shared 64-bit atomic minimum,
+// and finally writes each pixel it covered to the visibility buffer with one
+// global atomic minimum.  The minimum is order-independent, so the buffer is
+// the same as with k_stage3.
+
+// Shared memory of k_stage3_tiles: one 64-bit word per pixel of a tile.
+size_t stage3_tile_smem(uint32_t tile_log2) { return (size_t)8 << (2 * tile_log2); }
+
+// One block of kScanThreads: tile_start = exclusive prefix sum of tile_cnt
+// (and tile_start[n_tiles] = the total), tile_fill = tile_start, and the
+// list of tiles with parts (count in ctr->s3_tiles).
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_bin_scan(FrameDev f) {
+    __shared__ uint32_t wsum[kScanThreads / 32], wnz[kScanThreads / 32];
+    const uint32_t n = f.n_tiles;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t chunk = (n + kScanThreads - 1) / kScanThreads;
+    const uint32_t b = min(n, (uint32_t)t * chunk), e = min(n, b + chunk);
+    uint32_t sum = 0, nz = 0;
+    for (uint32_t g = b; g < e; ++g) {
+        const uint32_t c = f.tile_cnt[g];
+        sum += c;
+        nz += c != 0;
+    }
+    // block-wide exclusive scans of sum and nz
+    uint32_t is = sum, in = nz;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, is, o), c = __shfl_up_sync(0xffffffffu, in, o);
+        if (lane >= o) is += a, in += c;
+    }
+    if (lane == 31) wsum[warp] = is, wnz[warp] = in;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t a = wsum[lane], c = wnz[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, a, o), y = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) a += x, c += y;
+        }
+        wsum[lane] = a;
+        wnz[lane] = c;
+    }
+    __syncthreads();
+    uint32_t run = is - sum + (warp ? wsum[warp - 1] : 0u);
+    uint32_t at = in - nz + (warp ? wnz[warp - 1] : 0u);
+    for (uint32_t g = b; g < e; ++g) {
+        const uint32_t c = f.tile_cnt[g];
+        f.tile_start[g] = run;
+        f.tile_fill[g] = run;
+        if (c) f.tile_list[at++] = g;
+        run += c;
+    }
+    if (t == kScanThreads - 1) {
+        f.tile_start[n] = run;
+        f.ctr->s3_tiles = at;
+    }
+}
+
+// Queue-2 part indices into tile order.
+__global__ void __launch_bounds__(256) k_bin_scatter(FrameDev f) {
+    const unsigned long long total = *((volatile unsigned long long *)&f.ctr->q2_count);
+    const unsigned long long n = total < f.q2_cap ? total : f.q2_cap;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const Q2Entry &e = f.q2[i];
+        const ViewDev &vw = f.views[e.view];
+        const uint32_t g = vw.tile0 + e.ty * vw.ntx + e.tx;
+        f.part_sorted[atomicAdd(&f.tile_fill[g], 1u)] = (uint32_t)i;
+    }
+}
+
+// Shared-memory forms of the per-pixel writes of device.cuh: the closest
+// fragment wins by a 64-bit atomic minimum on the tile's word.
+__device__ __forceinline__ void tile_min(unsigned long long *w, uint64_t key) {
+    if (key < *w) atomicMin(w, (unsigned long long)key);
+}
+
+// i -> (i / w, i % w) for 0 <= i < 2^24 and 1 <= w <= 2^24: the float
+// quotient is within one of the exact one, so one correction step suffices.
+__device__ __forceinline__ void divmod_small(int i, int w, float rw, int &q, int &r) {
+    q = __float2int_rz(__fmul_rn(__int2float_rn(i), rw));
+    r = i - q * w;
+    if (r < 0) { --q; r += w; }
+    else if (r >= w) { ++q; r -= w; }
+}
+
+__global__ void __launch_bounds__(256) k_stage3_tiles(FrameDev f) {
+    extern __shared__ __align__(16) unsigned long long tw[];     // ts x ts words of the tile
+    __shared__ unsigned long long s_i;
+    const int tl = (int)f.tile_log2, ts = 1 << tl, npx = ts * ts;
+    const unsigned long long ntile = *((volatile unsigned long long *)&f.ctr->s3_tiles);
+    const int n_views = (int)f.hdr->n_views;
+    for (;;) {
+        if (threadIdx.x == 0) s_i = atomicAdd(&f.ctr->s3_next, 1ull);
+        for (int i = threadIdx.x; i < npx; i += blockDim.x) tw[i] = kEmpty;
+        __syncthreads();
+        const unsigned long long k = s_i;
+        if (k >= ntile) break;
+        const uint32_t g = f.tile_list[k];
+        int v = 0;
+        while (v + 1 < n_views && f.views[v + 1].tile0 <= g) ++v;
+        const ViewDev vw = f.views[v];
+        const uint32_t lt = g - vw.tile0;
+        const int ty = (int)(lt / vw.ntx), tx = (int)(lt - (uint32_t)ty * vw.ntx);
+        const int bx = tx * ts, by = ty * ts;
+        const uint32_t p0 = f.tile_start[g], p1 = f.tile_start[g + 1];
+        for (uint32_t p = p0; p < p1; ++p) {
+            const Q2Entry e = f.q2[f.part_sorted[p]];
+            if (e.ray) {
+                RayTri R;
+                if (!ray_tri_of(f, e.pair, e.id, R)) continue;
+                const int x0 = max(e.X[0], bx), x1 = min(e.X[1], bx + ts - 1);
+                const int y0 = max(e.Y[0], by), y1 = min(e.Y[1], by + ts - 1);
+                if (x0 > x1 || y0 > y1) continue;
+                const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+                const float rw = __frcp_rn(__int2float_rn(w));
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    int yy, xx;
+                    divmod_small(i, w, rw, yy, xx);
+                    const int x = x0 + xx, y = y0 + yy;
+                    uint64_t key;
+                    if (ray_key(R, x, y, vw, e.id, key)) tile_min(&tw[(y - by) * ts + (x - bx)], key);
+                }
+                continue;
+            }
+            SubTri s;
+            for (int c = 0; c < 3; ++c) { s.X[c] = e.X[c]; s.Y[c] = e.Y[c]; s.iz[c] = e.iz[c]; }
+            s.id = e.id;
+            if (!setup_subtri(s, vw.W, vw.H)) continue;
+            const int x0 = max(s.x0, bx), x1 = min(s.x1, bx + ts - 1);
+            const int y0 = max(s.y0, by), y1 = min(s.y1, by + ts - 1);
+            if (x0 > x1 || y0 > y1) continue;
+            const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+            const float rw = __frcp_rn(__int2float_rn(w));
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int yy, xx;
+                divmod_small(i, w, rw, yy, xx);
+                const int x = x0 + xx, y = y0 + yy;
+                uint64_t key;
+                if (pixel_key(s, x, y, key)) tile_min(&tw[(y - by) * ts + (x - bx)], key);
+            }
+        }
+        __syncthreads();
+        // one global atomic minimum per pixel the tile's parts covered
+        for (int i = threadIdx.x; i < npx; i += blockDim.x) {
+            const uint64_t key = tw[i];
+            if (key != kEmpty) {
+                const int x = bx + (i & (ts - 1)), y = by + (i >> tl);
+                depth_test_write(vw.vis, (size_t)y * (size_t)vw.W + (size_t)x, key);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // -------------------------------------------------------------- compare --
 __global__ void k_count_diff(const uint64_t *a, const uint64_t *b, uint64_t n, unsigned long long *out) {
     unsigned long long c = 0;
@@ -496,12 +660,28 @@ cudaError_t query_launch_shape(LaunchShape *o, int device) {
     if ((e = stage1_shape<true, false, false>(&o->stage1_blocks_per_sm[1][0])) != cudaSuccess) return e;
     if ((e = stage1_shape<true, true, false>(&o->stage1_blocks_per_sm[1][1])) != cudaSuccess) return e;
     if ((e = stage1_shape<true, false, true>(&o->stage1_blocks_per_sm[1][2])) != cudaSuccess) return e;
+    {
+        const size_t sw = stage1_win_smem_bytes();
+        e = cudaFuncSetAttribute(k_stage1_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sw);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1_blocks_per_sm[0][3], k_stage1_win, s1::kThreads, sw);
+        if (e != cudaSuccess) return e;
+        o->stage1_blocks_per_sm[1][3] = o->stage1_blocks_per_sm[0][3];
+    }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1x_blocks_per_sm, k_stage1_exact<false>,
                                                       32 * s1::kExactWarps, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage2_blocks_per_sm, k_stage2, 256, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage3_blocks_per_sm, k_stage3, 256, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_stage3_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage3_tile_smem(7));
+    if (e != cudaSuccess) return e;
+    for (int t = 4; t <= 7; ++t) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage3t_blocks_per_sm[t - 4], k_stage3_tiles, 256,
+                                                          stage3_tile_smem((uint32_t)t));
+        if (e != cudaSuccess) return e;
+    }
     return e;
 }
 
@@ -522,7 +702,8 @@ cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32
         else if (variant == 2) k_stage1<true, false, true><<<blocks, s1::kThreads, i0, s>>>(f, r);
         else k_stage1<true, false, false><<<blocks, s1::kThreads, i0, s>>>(f, r);
     } else {
-        if (variant == 1) k_stage1<false, true, false><<<blocks, s1::kThreads, s1f, s>>>(f, r);
+        if (variant == 3) k_stage1_win<<<blocks, s1::kThreads, stage1_win_smem_bytes(), s>>>(f, r);
+        else if (variant == 1) k_stage1<false, true, false><<<blocks, s1::kThreads, s1f, s>>>(f, r);
         else if (variant == 2) k_stage1<false, false, true><<<blocks, s1::kThreads, s0, s>>>(f, r);
         else k_stage1<false, false, false><<<blocks, s1::kThreads, s0, s>>>(f, r);
     }
@@ -542,6 +723,13 @@ cudaError_t launch_stage2(const FrameDev &f, int blocks, cudaStream_t s) {
 
 cudaError_t launch_stage3(const FrameDev &f, int blocks, cudaStream_t s) {
     k_stage3<<<blocks, 256, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage3_binned(const FrameDev &f, int scatter_blocks, int tile_blocks, cudaStream_t s) {
+    k_bin_scan<<<1, kScanThreads, 0, s>>>(f);
+    k_bin_scatter<<<scatter_blocks, 256, 0, s>>>(f);
+    k_stage3_tiles<<<tile_blocks, 256, stage3_tile_smem(f.tile_log2), s>>>(f);
     return cudaGetLastError();
 }
 

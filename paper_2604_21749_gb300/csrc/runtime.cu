@@ -228,6 +228,8 @@ curast_config default_config() {
     c.queue2_capacity = 1ull << 21;
     c.stage1_bitmap_bytes = 1ull << 32;
     c.stage1_group_min_pairs = 2;
+    c.stage1_vertex_reuse = 0;
+    c.stage3_tile_buffer = 1;
     c.check_indices = 1;
     c.collect_stats = 0;
     return c;
@@ -270,6 +272,9 @@ struct curast_ctx {
     std::vector<RoundDev> rounds;
     std::vector<char> round_comp;         // the round's meshes are compressed
     DevBuf<Q2Entry> d_q2;
+    DevBuf<uint32_t> d_sorted;            // queue-2 indices in tile order (binned stage 3)
+    DevBuf<uint32_t> d_tiles;             // per tile: count | start (+1) | fill | list
+    uint32_t n_tiles = 0;
     Counters *d_ctr = nullptr;
     unsigned *d_err = nullptr;
     float *d_aabb = nullptr;              // 256*6 scratch + 6 result
@@ -374,6 +379,8 @@ curast_status make_view(const curast_view &v, ViewDev *out) {
     out->hh = 0.5f * (float)v.H;
     out->W = v.W;
     out->H = v.H;
+    out->tile0 = 0;
+    out->ntx = 0;
     out->vis = v.vis;
     return CURAST_OK;
 }
@@ -482,6 +489,19 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
     uint64_t maxw = 1;
     for (const RoundDev &r : c->rounds) maxw = std::max(maxw, r.w1 - r.w0);
     CU(c->d_bits.reserve(maxw));
+    // stage-3 tiles of every view, numbered view by view, row by row
+    {
+        const uint64_t ts = 1ull << c->cfg.tile_log2;
+        uint64_t nt = 0;
+        for (ViewDev &v : c->hv) {
+            v.tile0 = (uint32_t)nt;
+            v.ntx = (uint32_t)(((uint64_t)v.W + ts - 1) / ts);
+            nt += (uint64_t)v.ntx * (((uint64_t)v.H + ts - 1) / ts);
+        }
+        if (nt >= (1ull << 31)) return CURAST_ERR_INVALID_ARG;
+        c->n_tiles = (uint32_t)nt;
+        if (c->cfg.stage3_tile_buffer) CU(c->d_tiles.reserve(4 * nt + 1));
+    }
     c->hdr.n_batches = nb;
     c->hdr.n_segs = (uint32_t)c->hs.size();
     c->hdr.n_views = (uint32_t)nv;
@@ -553,6 +573,16 @@ FrameDev make_frame_dev(const curast_ctx *c) {
     f.s3_ray = c->cfg.stage3_raycast;
     f.check = c->cfg.check_indices;
     f.stats = c->cfg.collect_stats;
+    f.s3_bin = c->cfg.stage3_tile_buffer;
+    f.n_tiles = c->n_tiles;
+    f.tile_cnt = f.tile_start = f.tile_fill = f.tile_list = f.part_sorted = nullptr;
+    if (f.s3_bin) {
+        f.tile_cnt = c->d_tiles.p;
+        f.tile_start = f.tile_cnt + c->n_tiles;
+        f.tile_fill = f.tile_start + c->n_tiles + 1;
+        f.tile_list = f.tile_fill + c->n_tiles;
+        f.part_sorted = c->d_sorted.p;
+    }
     return f;
 }
 
@@ -564,12 +594,13 @@ curast_status enqueue_stages(curast_ctx *c, bool clear, bool timing, cudaStream_
     if (clear)
         for (const ViewDev &v : c->hv) CU(launch_clear(v.vis, (uint64_t)v.W * (uint64_t)v.H, s));
     CU(cudaMemsetAsync(c->d_ctr, 0, sizeof(Counters), s));
+    if (f.s3_bin && c->n_tiles) CU(cudaMemsetAsync(f.tile_cnt, 0, (size_t)c->n_tiles * sizeof(uint32_t), s));
     if (timing) CU(cudaEventRecord(c->ev[1], s));
     // stage 1 round by round: the cull fills the survivor bitmap, the exact
     // kernel empties it (ev[2] falls after the last round's cull)
     const uint32_t nr = (uint32_t)c->rounds.size();
     for (uint32_t r = 0; r < nr; ++r) {
-        const int variant = c->round_comp[r] ? 2 : 0;
+        const int variant = c->round_comp[r] ? 2 : (!c->instanced && c->cfg.stage1_vertex_reuse ? 3 : 0);
         CU(launch_stage1(f, c->instanced, variant, r, sms * c->shape.stage1_blocks_per_sm[c->instanced ? 1 : 0][variant],
                          s));
         if (timing && r + 1 == nr) CU(cudaEventRecord(c->ev[2], s));
@@ -578,7 +609,10 @@ curast_status enqueue_stages(curast_ctx *c, bool clear, bool timing, cudaStream_
     if (timing) CU(cudaEventRecord(c->ev[3], s));
     CU(launch_stage2(f, sms * c->shape.stage2_blocks_per_sm, s));
     if (timing) CU(cudaEventRecord(c->ev[4], s));
-    CU(launch_stage3(f, sms * c->shape.stage3_blocks_per_sm, s));
+    if (f.s3_bin)
+        CU(launch_stage3_binned(f, sms * 4, sms * c->shape.stage3t_blocks_per_sm[c->cfg.tile_log2 - 4], s));
+    else
+        CU(launch_stage3(f, sms * c->shape.stage3_blocks_per_sm, s));
     if (timing) CU(cudaEventRecord(c->ev[5], s));
     c->ev_recorded = c->ev_recorded || timing;
     return CURAST_OK;
@@ -596,7 +630,8 @@ curast_status render_views(curast_ctx *c, const curast_view *views, int nv, long
     if (!graph) return enqueue_stages(c, clear, true, s);
     std::vector<uint64_t> key = {(uint64_t)nv, (uint64_t)c->instanced, (uint64_t)clear,
                                  (uint64_t)(uintptr_t)c->d_tab.p, (uint64_t)(uintptr_t)c->d_meshes.p,
-                                 (uint64_t)(uintptr_t)c->d_bits.p, (uint64_t)c->rounds.size()};
+                                 (uint64_t)(uintptr_t)c->d_bits.p, (uint64_t)c->rounds.size(),
+                                 (uint64_t)(uintptr_t)c->d_tiles.p, (uint64_t)(uintptr_t)c->d_sorted.p};
     for (char rc : c->round_comp) key.push_back((uint64_t)rc);
     for (int v = 0; v < nv; ++v) {
         key.push_back((uint64_t)views[v].W);
@@ -663,8 +698,10 @@ curast_status shade_setup(curast_ctx *c, const float *view, const float *proj, i
 curast_status alloc_queues(curast_ctx *c) {
     c->d_q1.release();
     c->d_q2.release();
+    c->d_sorted.release();
     CU(c->d_q1.reserve(std::max<uint64_t>(c->cfg.queue1_capacity, 1)));
     CU(c->d_q2.reserve(std::max<uint64_t>(c->cfg.queue2_capacity, 1)));
+    CU(c->d_sorted.reserve(std::max<uint64_t>(c->cfg.queue2_capacity, 1)));
     invalidate_graph(c);
     return CURAST_OK;
 }
@@ -763,7 +800,8 @@ bool valid_config(const curast_config &c) {
            c.pairs_per_segment >= 1 && c.pairs_per_segment <= 64 && c.queue1_capacity >= 1 &&
            c.queue2_capacity >= 1 && c.queue1_capacity <= (1ull << 32) && c.queue2_capacity <= (1ull << 32) &&
            c.stage1_bitmap_bytes >= (1ull << 12) && c.stage1_bitmap_bytes <= (1ull << 36) &&
-           c.stage1_group_min_pairs <= 64 && c.stage3_raycast <= 1 && c.stage1_exact_all <= 1 && c.reserved == 0;
+           c.stage1_group_min_pairs <= 64 && c.stage3_raycast <= 1 && c.stage1_exact_all <= 1 &&
+           c.stage1_vertex_reuse <= 1 && c.stage3_tile_buffer <= 1 && c.reserved == 0;
 }
 
 }  // namespace
@@ -838,6 +876,8 @@ void curast_destroy(curast_ctx *c) {
     c->h_tab.release();
     c->d_q1.release();
     c->d_q2.release();
+    c->d_sorted.release();
+    c->d_tiles.release();
     c->d_bits.release();
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->d_err) cudaFree(c->d_err);

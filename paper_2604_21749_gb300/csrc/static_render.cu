@@ -181,6 +181,8 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     fr.view.hh = 0.5f * (float)H;
     fr.view.W = W;
     fr.view.H = H;
+    fr.view.tile0 = 0;
+    fr.view.ntx = 0;
     fr.view.vis = vis;
     fr.mesh.pos = pos;
     fr.mesh.idx = idx;
@@ -215,6 +217,9 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     f.s3_ray = 0;
     f.check = 1;
     f.stats = 0;
+    f.s3_bin = 0;     // stage 3 writes straight to the buffer (no tile bins in the scratch)
+    f.n_tiles = 0;
+    f.tile_cnt = f.tile_start = f.tile_fill = f.tile_list = f.part_sorted = nullptr;
 
     const bool inst = n_instances > 1;
     const int sms = ds->shape.num_sms;

@@ -62,6 +62,8 @@ def test_small_workload_bit_exact_and_resolve(api, small):
     dict(queue1_capacity=1, queue2_capacity=1), dict(queue1_capacity=7, queue2_capacity=3),
     dict(stage1_bitmap_bytes=1 << 12), dict(stage1_bitmap_bytes=1 << 12, stage1_tri_per_thread=1),
     dict(stage1_exact_all=1), dict(stage1_exact_all=1, stage1_bitmap_bytes=1 << 12),
+    dict(stage1_vertex_reuse=1), dict(stage1_vertex_reuse=1, stage1_tri_per_thread=3),
+    dict(stage3_tile_buffer=0), dict(stage3_tile_buffer=0, tile_log2=4),
 ])
 def test_stage_choices_never_change_visibility(api, small, cfg):
     """Thresholds, tile size, batch shape and queue overflow move triangles
@@ -182,6 +184,73 @@ def test_per_mesh_launches_equal_oracle(api, mixed):
         r.sync()
         assert_vis_equal(vis, oracle_vis(mixed, c), f"per-mesh {c.W}x{c.H}")
     del keep
+
+
+def _permuted(mesh, seed):
+    """The same mesh with its triangles in a seeded random order (vertex
+    indices scattered over the whole mesh within every work item)."""
+    perm = np.random.default_rng(seed).permutation(mesh.idx.shape[0])
+    return Mesh(pos=mesh.pos, idx=mesh.idx[torch.from_numpy(perm)].contiguous(), rgba8=mesh.rgba8)
+
+
+@pytest.mark.parametrize("tpt", [4, 3, 1])
+def test_vertex_windows_edge_cases(api, tpt):
+    """The single-pair cull stages the vertex ranges of each work item in
+    shared memory.  Items that straddle grid rows (300 cells a row), a mesh
+    whose triangles come in random order (the windows are dropped), a
+    position buffer that starts off a 16-byte boundary (no bulk copy), a
+    mesh of 3 vertices (below the 4-vertex copy granule) and the 4-vertex
+    ground quad: each equal to the oracle, with and without vertex reuse."""
+    hf = S.heightfield_mesh(300, seed=100)
+    tiny = Mesh(pos=torch.tensor([[0.2, 0.01, 0.2], [0.8, 0.01, 0.3], [0.5, 0.02, 0.9]], dtype=torch.float32),
+                idx=torch.tensor([[0, 2, 1]], dtype=torch.int32))
+    meshes = [hf, _permuted(S.heightfield_mesh(150, seed=7), 3), tiny, S.ground_mesh()]
+    sc = Scene(meshes, [Instance(k, np.eye(4, dtype=np.float32)) for k in range(len(meshes))])
+    cams = [S.camera_unique_pose(k, 480, 270) for k in (0, 3, 6)]
+    refs = [oracle_vis(sc, c) for c in cams]
+    for reuse in (1, 0):
+        r = _renderer(api, stage1_tri_per_thread=tpt, stage1_vertex_reuse=reuse)
+        keep = []
+        for k, m in enumerate(meshes):
+            pos = m.pos.cuda().contiguous()
+            if k == 0:                               # the same floats, 4 bytes past a 16-byte boundary
+                buf = torch.empty(pos.numel() + 1, dtype=torch.float32, device="cuda")
+                buf[1:] = pos.reshape(-1)
+                pos = buf[1:].view(-1, 3)
+                assert pos.data_ptr() % 16 == 4
+            idx = m.idx.cuda().contiguous()
+            keep.append((pos, idx))
+            r.upload_mesh(pos, idx)
+        for it in sc.instances:
+            r.add_instance(it.mesh, it.model)
+        for c, ref in zip(cams, refs):
+            vis = r.render(c.view, c.proj, c.W, c.H)
+            r.sync()
+            assert_vis_equal(vis, ref, f"tpt {tpt} reuse {reuse} {c.W}x{c.H}")
+        del keep
+
+
+@pytest.mark.parametrize("tile_log2", [4, 6, 7])
+def test_stage3_tile_buffer_room_and_close_ups(api, tile_log2):
+    """Stage-3 workloads -- the camera inside a closed box (every face clipped
+    and split into tile parts over the whole screen) and close-up poses with
+    stage2_max_pixels = 32 (many mid-sized triangles, tens of parts a tile) --
+    with the shared-memory tile buffer and without it, each equal to the
+    oracle; with queue 2 of capacity 5 the overflow path joins in."""
+    room = S.scene_room()
+    hf = S.heightfield_mesh(300, seed=100)
+    close = Scene([hf], [Instance(0, np.eye(4, dtype=np.float32))], [])
+    cases = [(room, c) for c in room.cameras] + [(close, S.camera_unique_pose(k, 480, 270)) for k in (0, 3, 5)]
+    refs = [oracle_vis(sc, c) for sc, c in cases]
+    for cfg in (dict(stage3_tile_buffer=1), dict(stage3_tile_buffer=0), dict(stage3_tile_buffer=1, queue2_capacity=5)):
+        for (sc, c), ref in zip(cases, refs):
+            r = _renderer(api, tile_log2=tile_log2, stage2_max_pixels=32, collect_stats=1, **cfg)
+            keep = upload(r, sc)
+            vis = r.render(c.view, c.proj, c.W, c.H)
+            st = r.sync()
+            assert st["queued_stage3"] > 0
+            assert_vis_equal(vis, ref, f"{cfg} tile 2^{tile_log2} {c.W}x{c.H}")
+            del keep
 
 
 def test_unique_heightfield_poses_reduced(api):
