@@ -53,6 +53,10 @@ def parse_args():
                    help="skip the frame without the conservative cull (every triangle on the exact path)")
     p.add_argument("--no-diff", dest="diff", action="store_false",
                    help="skip the differentiable interpolation step (forward and backward)")
+    p.add_argument("--no-resolve", dest="resolve", action="store_false",
+                   help="skip timing the resolve and the textured resolve of the frame")
+    p.add_argument("--no-unique", dest="unique", action="store_false",
+                   help="skip the 100M-triangle heightfield's 8 poses at 1920x1080 and 3840x2160")
     p.add_argument("--no-raycast", dest="raycast", action="store_false",
                    help="skip the stage-3 workloads timed with the fixed-point rule and with the ray cast")
     p.add_argument("--subset", type=int, default=0,
@@ -224,6 +228,54 @@ def _cpu_sample(tiles: int, cells: int, frac: float, count: int):
     return _CPU_SAMPLES[key]
 
 
+def _all_core_worker(k, tiles, cells, W, H, barrier, queue):
+    """One process of the all-core CPU baseline: generates tile k, waits for
+    every process, then renders it with the oracle (ids numbered over all
+    tiles) and reports (triangles, seconds)."""
+    import torch
+    torch.set_num_threads(1)
+    sys.path.insert(0, ROOT)
+    import synthetic as S
+    from oracle import oracle as orc
+    cam = S.camera_billion(W, H, tiles)
+    sc = S.scene_billion(tiles=tiles, n=cells, only=[k], colours=False)
+    osc = orc.OracleScene(sc, tri_counts=[2 * cells * cells] * (tiles * tiles))
+    import numpy as np
+    out = np.full((H, W), orc.EMPTY, np.uint64)
+    barrier.wait()
+    t0 = time.perf_counter()
+    orc.render(osc, cam, first=k, count=1, out=out)
+    queue.put((2 * cells * cells, time.perf_counter() - t0))
+
+
+def cpu_baseline_all_cores(args):
+    """The oracle on every host core at once: one process per core (spawned,
+    each single-threaded), each rendering one central tile of the frame after
+    all have generated theirs; Gtris/s = all their triangles over the
+    slowest process's render time (the per-tile buffers would be merged by an
+    element-wise minimum, which is not timed)."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    n = min(ncores, args.tiles * args.tiles)
+    cx = cz = args.tiles / 2.0
+    order = sorted(range(args.tiles * args.tiles),
+                   key=lambda k: (k % args.tiles + 0.5 - cx) ** 2 + (k // args.tiles + 0.5 - cz) ** 2)
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(n), ctx.Queue()
+    procs = [ctx.Process(target=_all_core_worker, args=(k, args.tiles, args.cells, args.W, args.H, barrier, queue))
+             for k in order[:n]]
+    for p in procs:
+        p.start()
+    res = [queue.get(timeout=600) for _ in procs]
+    for p in procs:
+        p.join()
+    tris = sum(t for t, _ in res)
+    slowest = max(s for _, s in res)
+    return {"value": round(tris / slowest / 1e9, 5), "unit": "Gtris/s", "cores": n, "kind": "oracle",
+            "sample": f"{n} central tiles ({tris} triangles) of the same frame, one single-threaded oracle "
+                      f"process per core, slowest {slowest:.1f} s"}
+
+
 def cpu_baseline_sample(tiles: int, cells: int, W: int, H: int, frac: float = 1.0, count: int = 1):
     """Times the oracle (single thread) on `count` central tiles of the
     terrain, or on the first `frac` of one tile's triangles; returns
@@ -364,10 +416,15 @@ def run_ours(args, ranks: Ranks):
         "e2e": {"value": round(total_tris / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gtris/s",
                 "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": args.W * args.H * 4},
-        "gpu_launches": (3 + 2 * info["rounds"]) * args.steps,
+        # per frame: clear, a cull and an exact kernel per round, stage 2, and
+        # stage 3 as scan + scatter + tile kernels
+        "gpu_launches": (5 + 2 * info["rounds"]) * args.steps,
         "clocks": clk,
         "frame_stats": {k: v for k, v in stats.items() if v},
     }
+    if ranks.rank == 0 and ranks.world == 1 and args.resolve:
+        result["resolve"] = resolve_timing(r, cam, args, vis, stream)
+        result["resolve_textured"] = resolve_textured_timing(r, sc, cam, args, vis, stream)
     if ranks.rank == 0 and ranks.world == 1 and args.supersampling:
         result["supersampling"] = supersampling(r, cam, args, ms_frame, stream)
     if ranks.rank == 0 and ranks.world == 1 and args.ablation:
@@ -378,6 +435,8 @@ def run_ours(args, ranks: Ranks):
     del sc, vis
     torch.cuda.empty_cache()
 
+    if ranks.rank == 0 and ranks.world == 1 and args.unique:
+        result["unique_100m"] = unique_100m(args, dev)
     if ranks.rank == 0 and ranks.world == 1 and args.raycast:
         result["raycast_stage3"] = raycast_stage3(args, dev)
     if ranks.rank == 0 and ranks.world == 1 and args.diff:
@@ -389,6 +448,8 @@ def run_ours(args, ranks: Ranks):
         result["cpu_baseline"] = {"value": round(g, 5), "unit": "Gtris/s", "cores": 1, "kind": "oracle",
                                   "sample": f"three adjacent central tiles ({n} triangles) of the same frame, "
                                             f"single-threaded oracle, {dt:.1f} s"}
+        result["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args)
+    result["config"]["host_cores"] = os.cpu_count()
     return result
 
 
@@ -435,6 +496,132 @@ def compressed_frame(args, sc, cam, dev, stream, info_plain, ms_plain):
             "uncompressed_bytes_read": round(plain_bytes),
             "cull_gbs": round(read_bytes / (cull_ms * 1e-3) / 1e9, 1),
             "triangles_per_frame": info["triangles"]}
+
+
+def _time_calls(fn, stream, reps):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def resolve_timing(r, cam, args, vis, stream):
+    """The resolve of the frame (Section 4.4) on its own: FP32 RGBA and RGBA8
+    out, ms per call, and its roofline.  Algorithmic bytes: the 8-byte word
+    read and 16 + 4 bytes written per pixel, plus per covered pixel the
+    triangle's 12 bytes of indices, 36 of positions and 12 of vertex colours
+    gathered."""
+    import torch
+    from paper_2604_21749_gb300 import api
+    H, W = vis.shape
+    f32 = torch.empty((H, W, 4), dtype=torch.float32, device=vis.device)
+    u8 = torch.empty((H, W, 4), dtype=torch.uint8, device=vis.device)
+    vm, pm = api._mat(cam.view), api._mat(cam.proj)
+
+    def call():
+        api._check(r.L.curast_resolve(r._h, vm, pm, W, H, api._ptr(vis), api._ptr(f32), api._ptr(u8),
+                                      api._stream()), "curast_resolve")
+
+    ms = _time_calls(call, stream, 20)
+    covered = int((vis != -1).sum().item())
+    nbytes = W * H * (8 + 20) + covered * (12 + 36 + 12)
+    peak, kind = measured_peaks()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"ms": round(ms, 4), "pixels": W * H, "covered": covered,
+            "roofline": {"bound": "hbm", "kernel": "k_resolve", "achieved": round(gbs, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_kind": kind,
+                         "bytes_per_launch": nbytes,
+                         "bytes_rule": "8 B read + 20 B written per pixel, 60 B gathered per covered pixel"}}
+
+
+def resolve_textured_timing(r, sc, cam, args, vis, stream):
+    """The textured resolve of the frame (Section 4.4, mip level from four
+    pixel rays): every tile textured with one shared 4096^2 RGBA8 mip chain
+    over its unit square (uv = the grid coordinates), ms per call and the
+    histogram of the levels chosen."""
+    import torch
+    import synthetic as S
+    H, W = vis.shape
+    n = int(round(math.sqrt(sc.meshes[0].V))) - 1
+    uv = S.grid_uv(n, device=vis.device)
+    tex = S.texture_mip_chain(12, seed=9, device=vis.device)
+    for k, m in enumerate(sc.meshes):
+        if m.T > 0 and m.V == uv.shape[0]:
+            r.set_mesh_texture(k, uv, tex, 12)
+    f32 = torch.empty((H, W, 4), dtype=torch.float32, device=vis.device)
+    u8 = torch.empty((H, W, 4), dtype=torch.uint8, device=vis.device)
+    lev = torch.empty((H, W), dtype=torch.uint8, device=vis.device)
+    from paper_2604_21749_gb300 import api
+    vm, pm = api._mat(cam.view), api._mat(cam.proj)
+
+    def call():
+        api._check(r.L.curast_resolve_textured(r._h, vm, pm, W, H, api._ptr(vis), api._ptr(f32), api._ptr(u8),
+                                               api._ptr(lev), api._stream()), "curast_resolve_textured")
+
+    ms = _time_calls(call, stream, 20)
+    hist = torch.bincount(lev.reshape(-1).to(torch.int64), minlength=256)
+    levels = {str(k): int(hist[k]) for k in range(13) if hist[k] > 0}
+    for k, m in enumerate(sc.meshes):
+        r.set_mesh_texture(k, None, None)
+    del uv, tex, f32, u8, lev
+    torch.cuda.empty_cache()
+    return {"ms": round(ms, 4), "texture": "4096^2 RGBA8 with its 13-level mip chain, uv = grid coordinates",
+            "levels": levels}
+
+
+def unique_100m(args, dev):
+    """The 100M-triangle heightfield (7072^2 cells, one mesh): its 8 seeded
+    poses, whole-mesh views to close-ups, at 1920x1080 and 3840x2160; per
+    pose frame ms, Gtris/s and per-stage ms."""
+    import torch
+    import numpy as np
+    import synthetic as S
+    from paper_2604_21749_gb300 import api
+    t0 = time.perf_counter()
+    sc = S.scene_unique(device=dev)
+    torch.cuda.synchronize()
+    tgen = time.perf_counter() - t0
+    m = sc.meshes[0]
+    r = api.Renderer(dev.index)
+    r.upload_mesh(m.pos, m.idx, m.rgba8)
+    r.add_instance(0, np.eye(4, dtype=np.float32))
+    stream = torch.cuda.current_stream()
+    poses = []
+    for W, H in ((1920, 1080), (3840, 2160)):
+        vis = r.new_vis(W, H)
+        for k in range(8):
+            cam = S.camera_unique_pose(k, W, H)
+            st = []
+
+            def frame():
+                r.render(cam.view, cam.proj, W, H, vis)
+
+            ms = _time_calls(frame, stream, 10)
+            frame()
+            st = r.stage_times()
+            info = r.last_frame()
+            poses.append({"pose": k, "W": W, "H": H, "frame_ms": round(ms, 4),
+                          "gtris_s": round(info["triangles"] / (ms * 1e-3) / 1e9, 2),
+                          "stage_ms": {n: round(v, 4) for n, v in
+                                       zip(["clear", "stage1_cull", "stage1_exact", "stage2", "stage3"], st)}})
+        del vis
+    r.set_config(collect_stats=1)
+    cam = S.camera_unique_pose(7, 3840, 2160)
+    r.render(cam.view, cam.proj, 3840, 2160)
+    stats = r.sync()
+    r.close()
+    del sc, m
+    torch.cuda.empty_cache()
+    return {"workload": f"100M unique: heightfield of 7072^2 cells ({2 * 7072 ** 2} triangles), 8 poses",
+            "generation_s": round(tgen, 2), "poses": poses,
+            "pose7_3840x2160_stats": {k: v for k, v in stats.items() if v}}
 
 
 def conservative_cull_ablation(r, cam, args, ms_on, vis, stream):
@@ -535,7 +722,10 @@ def raycast_stage3(args, dev):
     the paper's ray-cast stage 3 (stage3_raycast): the camera inside a closed
     box at the frame size (every face huge and crossing the near plane), and
     a close-up pose of a 1448^2 heightfield with stage2_max_pixels = 32 so
-    that its large triangles are ray cast.  Frame ms and stage-3 ms of each."""
+    that its large triangles are ray cast.  Each with the shared-memory tile
+    buffer of stage 3 (default) and with every covered pixel written to the
+    global buffer (stage3_tile_buffer = 0, keys *_global_writes).  Frame ms
+    and per-stage ms of each."""
     import numpy as np
     import torch
     import synthetic as S
@@ -557,8 +747,8 @@ def raycast_stage3(args, dev):
             r.add_instance(it.mesh, it.model)
         vis = r.new_vis(cam.W, cam.H)
         row = {"workload": name}
-        for mode in (0, 1):
-            r.set_config(stage3_raycast=mode, **cfg)
+        for mode, tb in ((0, 1), (1, 1), (0, 0), (1, 0)):
+            r.set_config(stage3_raycast=mode, stage3_tile_buffer=tb, **cfg)
             for _ in range(3):
                 r.render(cam.view, cam.proj, cam.W, cam.H, vis)
             r.sync()
@@ -571,7 +761,7 @@ def raycast_stage3(args, dev):
             torch.cuda.synchronize()
             r.render(cam.view, cam.proj, cam.W, cam.H, vis)
             st = r.stage_times()
-            key = "ray_cast" if mode else "fixed_point"
+            key = ("ray_cast" if mode else "fixed_point") + ("" if tb else "_global_writes")
             row[key + "_ms"] = round(e0.elapsed_time(e1) / frames, 4)
             row[key + "_stage_ms"] = {k: round(v, 4) for k, v in
                                       zip(["clear", "stage1_cull", "stage1_exact", "stage2", "stage3"], st)}

@@ -112,12 +112,13 @@ typedef struct {
                                     reuse); 0 (default): every triangle gathers and
                                     transforms its three vertices, which runs faster on
                                     GB300 (the result is the same)                           */
-    uint32_t stage3_tile_buffer; /* 1 (default): stage 3 sorts its tile parts by tile and
-                                    gives each tile a shared-memory framebuffer (Section
-                                    4.3): the parts of a tile meet there, and each covered
-                                    pixel takes one global atomic minimum; 0: every covered
-                                    pixel of every part goes to the global buffer (the
-                                    result is the same)                                     */
+    uint32_t stage3_tile_buffer; /* 1: stage 3 sorts its tile parts by tile and gives each
+                                    tile a shared-memory framebuffer (Section 4.3): up to 8
+                                    parts of a tile meet there, and each covered pixel takes
+                                    one global atomic minimum; 0 (default, faster on most of
+                                    the workloads measured): every covered pixel of every
+                                    part goes to the global buffer after a plain read (the
+                                    result is the same)                                      */
     uint32_t reserved;           /* 0                                                        */
 } curast_config;
 
@@ -266,6 +267,36 @@ curast_status curast_resolve(curast_ctx *ctx, const float view[16], const float 
  * 16384; ss = 1 is curast_resolve.  Buffers as for curast_resolve. */
 curast_status curast_resolve_ss(curast_ctx *ctx, const float view[16], const float proj[16], int W, int H, int ss,
                                 const uint64_t *vis, float *rgba_f32, uint8_t *rgba8, curast_stream stream);
+
+/* Textured resolve (Section 4.4 "Shading and Mip Mapping").  Registers a
+ * texture for a mesh:
+ *   uv      device, V x 2 FP32 texture coordinates (8-byte aligned)
+ *   texels  device, a square RGBA8 texture of side 2^log2_size with its whole
+ *           mip chain: level l (0 .. log2_size) holds (2^(log2_size - l))^2
+ *           texels, row-major with row 0 at v = 0, each level right after
+ *           the one before (4-byte aligned); NULL removes the texture
+ *   log2_size  0..15
+ * Both buffers are BORROWED like the mesh's: they must stay allocated and
+ * unchanged while resolves that use them run.  Fails with
+ * CURAST_ERR_INVALID_ARG for a bad mesh id, size or alignment. */
+curast_status curast_set_mesh_texture(curast_ctx *ctx, uint32_t mesh_id, const float *uv, const uint8_t *texels,
+                                      int log2_size);
+
+/* Screen pass with textures: as curast_resolve, but pixels of a textured
+ * mesh take their colour from the texture.  Rays through the centres of the
+ * pixel and of its right (x + 1), top (y + 1) and top-right neighbours meet
+ * the plane of the pixel's triangle; their barycentrics (unclamped, so
+ * points off the triangle extrapolate) interpolate the vertex uv; the
+ * footprint F is the larger side of the four samples' uv bounding box times
+ * 2^log2_size, and the mip level is floor(log2 F) clamped to 0..log2_size
+ * (0 when F < 1).  The colour is the nearest texel of that level at the
+ * pixel's own uv -- column floor(u s), row floor(v s), s the level's side,
+ * clamped to the level -- as byte / 255.  rgba_f32 (16-byte aligned),
+ * rgba8 (4-byte aligned) and level (W*H bytes: the level per pixel, 255 for
+ * background and untextured pixels) are device buffers or NULL. */
+curast_status curast_resolve_textured(curast_ctx *ctx, const float view[16], const float proj[16], int W, int H,
+                                      const uint64_t *vis, float *rgba_f32, uint8_t *rgba8, uint8_t *level,
+                                      curast_stream stream);
 
 /* --------------------------------------------------- differentiable step --- */
 

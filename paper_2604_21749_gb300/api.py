@@ -28,7 +28,8 @@ EXPORTS = ["curast_create", "curast_destroy", "curast_status_string", "curast_ge
            "curast_upload_mesh", "curast_update_mesh", "curast_add_instance", "curast_clear_instances",
            "curast_clear", "curast_render", "curast_render_mesh", "curast_render_batch", "curast_resolve", "curast_resolve_ss", "curast_get_mesh_info",
            "curast_interpolate", "curast_interpolate_backward", "curast_sync", "curast_stage_times",
-           "curast_autotune", "curast_last_frame", "curast_render_static"]
+           "curast_autotune", "curast_last_frame", "curast_render_static", "curast_set_mesh_texture",
+           "curast_resolve_textured"]
 
 
 class CurastError(RuntimeError):
@@ -125,6 +126,8 @@ def load(build: bool = False, path: Optional[str] = None) -> C.CDLL:
             "curast_render_batch": [vp, C.POINTER(View), i32, i32, vp],
             "curast_resolve": [vp, fp, fp, i32, i32, vp, vp, vp, vp],
             "curast_resolve_ss": [vp, fp, fp, i32, i32, i32, vp, vp, vp, vp],
+            "curast_set_mesh_texture": [vp, u32, vp, vp, i32],
+            "curast_resolve_textured": [vp, fp, fp, i32, i32, vp, vp, vp, vp, vp],
             "curast_interpolate": [vp, u32, vp, fp, fp, i32, i32, vp, vp, i32, vp, vp],
             "curast_interpolate_backward": [vp, u32, vp, fp, fp, i32, i32, vp, vp, i32, vp, vp, vp, vp],
             "curast_sync": [vp, vp, C.POINTER(Stats)],
@@ -323,6 +326,37 @@ class Renderer:
         _check(self.L.curast_resolve_ss(self._h, _mat(view), _mat(proj), W, H, ss, _ptr(vis), _ptr(f32), _ptr(u8),
                                         _stream(stream)), "curast_resolve_ss")
         return f32, u8
+
+    def set_mesh_texture(self, mesh: int, uv: Optional[torch.Tensor], texels: Optional[torch.Tensor],
+                         log2_size: int = 0):
+        """Per-vertex uv (V, 2) float32 and a flat RGBA8 mip chain of side
+        2^log2_size for the textured resolve; texels=None removes it.  The
+        tensors are kept referenced while registered."""
+        if texels is None:
+            _check(self.L.curast_set_mesh_texture(self._h, mesh, None, None, 0), "curast_set_mesh_texture")
+            self._keep.pop(("tex", mesh), None)
+            return
+        _need(uv, torch.float32, "uv", self.device)
+        _need(texels, torch.uint8, "texels", self.device)
+        want = 4 * sum(4 ** (log2_size - l) for l in range(log2_size + 1))
+        if texels.numel() != want:
+            raise ValueError(f"a mip chain of side 2^{log2_size} holds {want} bytes, got {texels.numel()}")
+        _check(self.L.curast_set_mesh_texture(self._h, mesh, _ptr(uv), _ptr(texels), log2_size),
+               "curast_set_mesh_texture")
+        self._keep[("tex", mesh)] = (uv, texels)
+
+    def resolve_textured(self, view, proj, vis: torch.Tensor, want_f32: bool = True, want_rgba8: bool = True,
+                         want_level: bool = True, stream=None):
+        """Resolve with textures and the 4-ray mip-level choice; returns
+        (rgba float32 (H, W, 4), rgba8 (H, W, 4), level uint8 (H, W)), each
+        None when not wanted."""
+        H, W = vis.shape
+        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device) if want_f32 else None
+        u8 = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device) if want_rgba8 else None
+        lev = torch.empty((H, W), dtype=torch.uint8, device=self.device) if want_level else None
+        _check(self.L.curast_resolve_textured(self._h, _mat(view), _mat(proj), W, H, _ptr(vis), _ptr(f32), _ptr(u8),
+                                              _ptr(lev), _stream(stream)), "curast_resolve_textured")
+        return f32, u8, lev
 
     # ------------------------------------------------------- differentiable
     def interpolate(self, mesh: int, view, proj, vis: torch.Tensor, attr: torch.Tensor,

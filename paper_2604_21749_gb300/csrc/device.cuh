@@ -42,7 +42,10 @@ struct PairDev {             // one (instance, view) pair that survived host cul
     float wsafe, win;
     // bound on the rounding of a row evaluated anywhere in the mesh bounds,
     // for the X'*w, Y'*w and w rows (2^-19 times the row's magnitude bound)
-    float fs[3], pad;
+    float fs[3];
+    // near-plane cull: a vertex whose estimated w (the w row) lies below nlo
+    // has an exact w below the near plane; -inf disables the test
+    float nlo;
     uint64_t base;           // global id of the instance's triangle 0
     uint32_t view;
     uint32_t mesh;
@@ -77,6 +80,11 @@ struct MeshDev {
     const uint16_t *qpos;
     uint32_t bits, mask, imin, pad;
     float lo[3], step[3];
+    // texture of the textured resolve (Section 4.4): per-vertex uv (V x 2)
+    // and a square RGBA8 mip chain of side 2^tex_log2; uv == nullptr: none
+    const float *uv;
+    const uint8_t *tex;
+    int32_t tex_log2, pad2;
 };
 
 __device__ __forceinline__ bool compressed(const MeshDev &m) { return m.cidx != nullptr; }
@@ -126,7 +134,7 @@ struct Counters {
     unsigned int error, pad;
     unsigned long long stats[8];      // see Stat
     unsigned long long s3_next;       // binned stage 3: tiles taken
-    unsigned long long s3_tiles;      // binned stage 3: tiles with at least one part
+    unsigned long long s3_tiles;      // binned stage 3: units of work (parts of one tile)
 };
 
 enum Stat { kStatIn = 0, kStatClip, kStatBack, kStatTiny, kStatS1, kStatS2, kStatParts, kStatFast, kStatCount };
@@ -168,7 +176,7 @@ struct FrameDev {
     uint32_t *tile_cnt;      // n_tiles: parts per tile (counted by stage 2)
     uint32_t *tile_start;    // n_tiles + 1: exclusive prefix sum of tile_cnt
     uint32_t *tile_fill;     // n_tiles: scatter cursors
-    uint32_t *tile_list;     // tiles with at least one part
+    uint2 *units;            // (tile, first part in part_sorted): up to 8 parts of one tile
     uint32_t *part_sorted;   // q2_cap: queue-2 indices in tile order
 };
 

@@ -21,7 +21,10 @@ cudaError_t query_launch_shape(LaunchShape *out, int device);
 cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s);
 // Stage 1 of round r: the cull kernel (fused: it runs the exact path itself
 // and needs no bitmap), then the exact kernel over the round's bitmap.
-cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32_t r, int blocks, cudaStream_t s);
+// near = false launches the single-pair cull without its near-plane test
+// (valid when no pair's mesh bounds reach the near plane).
+cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32_t r, int blocks, bool near,
+                          cudaStream_t s);
 cudaError_t launch_stage1_exact(const FrameDev &f, uint32_t r, int blocks, cudaStream_t s);
 cudaError_t launch_stage2(const FrameDev &f, int blocks, cudaStream_t s);
 cudaError_t launch_stage3(const FrameDev &f, int blocks, cudaStream_t s);
@@ -52,6 +55,7 @@ struct ShadeArgs {
     float *rgba_f32;
     uint8_t *rgba8;
     int ss;                     // super-sampled resolve: samples per pixel axis
+    uint8_t *level;             // textured resolve: the mip level per pixel (255: none), or null
     // interpolate
     uint32_t mesh;
     const float *pos;           // overrides the mesh's positions when non-null
@@ -66,6 +70,8 @@ struct ShadeArgs {
 cudaError_t launch_resolve(const ShadeArgs &a, cudaStream_t s);
 // a.W, a.H: the super-sampled buffer (ss W x ss H); W, H: the output
 cudaError_t launch_resolve_ss(const ShadeArgs &a, int W, int H, cudaStream_t s);
+// resolve with textures and the 4-ray mip-level choice (Section 4.4)
+cudaError_t launch_resolve_textured(const ShadeArgs &a, cudaStream_t s);
 cudaError_t launch_interpolate(const ShadeArgs &a, cudaStream_t s);
 cudaError_t launch_interpolate_backward(const ShadeArgs &a, cudaStream_t s);
 

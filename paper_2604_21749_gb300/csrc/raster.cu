@@ -440,59 +440,61 @@ __global__ void __launch_bounds__(256) k_stage3(FrameDev f) {
 // ------------------------------------------------------- binned stage 3 --
 // Section 4.3 with the tile framebuffer in shared memory: the parts stage 2
 // queued are sorted by tile (stage 2 counts them per tile; one block scans
-// the counts; a scatter pass writes the part indices in tile order), then one
-// block takes one tile at a time, keeps the tile's words in shared memory,
-// applies every part of the tile there with a shared 64-bit atomic minimum,
-// and finally writes each pixel it covered to the visibility buffer with one
-// global atomic minimum.  The minimum is order-independent, so the buffer is
-// the same as with k_stage3.
+// the counts; a scatter pass writes the part indices in tile order) and cut
+// into units of at most kUnitParts parts of one tile.  A block takes one
+// unit at a time: it keeps the tile's words in shared memory, applies all of
+// the unit's parts there, and then writes each pixel they covered to the
+// visibility buffer with one global atomic minimum.  The minimum is
+// order-independent, so the buffer is the same as with k_stage3.
+constexpr int kUnitParts = 8;
 
 // Shared memory of k_stage3_tiles: one 64-bit word per pixel of a tile.
 size_t stage3_tile_smem(uint32_t tile_log2) { return (size_t)8 << (2 * tile_log2); }
 
 // One block of kScanThreads: tile_start = exclusive prefix sum of tile_cnt
-// (and tile_start[n_tiles] = the total), tile_fill = tile_start, and the
-// list of tiles with parts (count in ctr->s3_tiles).
+// (tile_start[n_tiles] = the total), tile_fill = tile_start, and the units
+// (tile, first part) of every tile, ceil(count / kUnitParts) each (their
+// number in ctr->s3_tiles).
 constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) k_bin_scan(FrameDev f) {
-    __shared__ uint32_t wsum[kScanThreads / 32], wnz[kScanThreads / 32];
+    __shared__ uint32_t wsum[kScanThreads / 32], wnu[kScanThreads / 32];
     const uint32_t n = f.n_tiles;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t chunk = (n + kScanThreads - 1) / kScanThreads;
     const uint32_t b = min(n, (uint32_t)t * chunk), e = min(n, b + chunk);
-    uint32_t sum = 0, nz = 0;
+    uint32_t sum = 0, nu = 0;
     for (uint32_t g = b; g < e; ++g) {
         const uint32_t c = f.tile_cnt[g];
         sum += c;
-        nz += c != 0;
+        nu += (c + kUnitParts - 1) / kUnitParts;
     }
-    // block-wide exclusive scans of sum and nz
-    uint32_t is = sum, in = nz;
+    // block-wide exclusive scans of sum and nu
+    uint32_t is = sum, iu = nu;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t a = __shfl_up_sync(0xffffffffu, is, o), c = __shfl_up_sync(0xffffffffu, in, o);
-        if (lane >= o) is += a, in += c;
+        const uint32_t a = __shfl_up_sync(0xffffffffu, is, o), c = __shfl_up_sync(0xffffffffu, iu, o);
+        if (lane >= o) is += a, iu += c;
     }
-    if (lane == 31) wsum[warp] = is, wnz[warp] = in;
+    if (lane == 31) wsum[warp] = is, wnu[warp] = iu;
     __syncthreads();
     if (warp == 0) {
-        uint32_t a = wsum[lane], c = wnz[lane];
+        uint32_t a = wsum[lane], c = wnu[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t x = __shfl_up_sync(0xffffffffu, a, o), y = __shfl_up_sync(0xffffffffu, c, o);
             if (lane >= o) a += x, c += y;
         }
         wsum[lane] = a;
-        wnz[lane] = c;
+        wnu[lane] = c;
     }
     __syncthreads();
     uint32_t run = is - sum + (warp ? wsum[warp - 1] : 0u);
-    uint32_t at = in - nz + (warp ? wnz[warp - 1] : 0u);
+    uint32_t at = iu - nu + (warp ? wnu[warp - 1] : 0u);
     for (uint32_t g = b; g < e; ++g) {
         const uint32_t c = f.tile_cnt[g];
         f.tile_start[g] = run;
         f.tile_fill[g] = run;
-        if (c) f.tile_list[at++] = g;
+        for (uint32_t q = 0; q < c; q += kUnitParts) f.units[at++] = make_uint2(g, run + q);
         run += c;
     }
     if (t == kScanThreads - 1) {
@@ -514,84 +516,117 @@ __global__ void __launch_bounds__(256) k_bin_scatter(FrameDev f) {
     }
 }
 
-// Shared-memory forms of the per-pixel writes of device.cuh: the closest
-// fragment wins by a 64-bit atomic minimum on the tile's word.
-__device__ __forceinline__ void tile_min(unsigned long long *w, uint64_t key) {
-    if (key < *w) atomicMin(w, (unsigned long long)key);
-}
+// One part of a unit, set up once for all of the unit's threads.
+struct PartRec {
+    SubTri s;                // fixed-point rule; s.x0..s.y1: the pixel range clamped to the tile
+    RayTri R;                // ray-cast parts
+    int ray;
+};
 
-// i -> (i / w, i % w) for 0 <= i < 2^24 and 1 <= w <= 2^24: the float
-// quotient is within one of the exact one, so one correction step suffices.
-__device__ __forceinline__ void divmod_small(int i, int w, float rw, int &q, int &r) {
-    q = __float2int_rz(__fmul_rn(__int2float_rn(i), rw));
-    r = i - q * w;
-    if (r < 0) { --q; r += w; }
-    else if (r >= w) { ++q; r -= w; }
-}
-
+// Thread t of the block owns the pixels (t mod ts, t / ts + k 256 / ts),
+// k = 0 .. ts^2 / 256 - 1, of the tile (tile-local coordinates; ts >= 16),
+// and only it touches their words, so the minimum there needs no atomic.
+// For every part of the unit the thread walks its own pixels inside the
+// part's range -- one column, every (256 / ts)-th row -- with the edge
+// functions stepped from row to row; then it writes each of its covered
+// pixels once to the visibility buffer and resets the word.
 __global__ void __launch_bounds__(256) k_stage3_tiles(FrameDev f) {
-    extern __shared__ __align__(16) unsigned long long tw[];     // ts x ts words of the tile
+    extern __shared__ __align__(16) unsigned long long tw[];     // the tile's words
+    __shared__ PartRec pr[kUnitParts];
     __shared__ unsigned long long s_i;
-    const int tl = (int)f.tile_log2, ts = 1 << tl, npx = ts * ts;
-    const unsigned long long ntile = *((volatile unsigned long long *)&f.ctr->s3_tiles);
+    const int tl = (int)f.tile_log2, ts = 1 << tl;
+    const unsigned long long nunit = *((volatile unsigned long long *)&f.ctr->s3_tiles);
     const int n_views = (int)f.hdr->n_views;
+    const int tid = threadIdx.x;
+    const int lx = tid & (ts - 1), ly0 = tid >> tl, dyr = 256 >> tl;   // my column, first row, row step
+    for (int i = tid; i < ts * ts; i += 256) tw[i] = kEmpty;     // (each thread's own pixels)
     for (;;) {
-        if (threadIdx.x == 0) s_i = atomicAdd(&f.ctr->s3_next, 1ull);
-        for (int i = threadIdx.x; i < npx; i += blockDim.x) tw[i] = kEmpty;
+        if (tid == 0) s_i = atomicAdd(&f.ctr->s3_next, 1ull);
         __syncthreads();
         const unsigned long long k = s_i;
-        if (k >= ntile) break;
-        const uint32_t g = f.tile_list[k];
+        if (k >= nunit) break;
+        const uint2 u = f.units[k];
+        const uint32_t g = u.x, p0 = u.y, p1 = min(p0 + (uint32_t)kUnitParts, f.tile_start[g + 1]);
+        const int np = (int)(p1 - p0);
         int v = 0;
         while (v + 1 < n_views && f.views[v + 1].tile0 <= g) ++v;
-        const ViewDev vw = f.views[v];
+        const ViewDev &vw = f.views[v];
         const uint32_t lt = g - vw.tile0;
         const int ty = (int)(lt / vw.ntx), tx = (int)(lt - (uint32_t)ty * vw.ntx);
         const int bx = tx * ts, by = ty * ts;
-        const uint32_t p0 = f.tile_start[g], p1 = f.tile_start[g + 1];
-        for (uint32_t p = p0; p < p1; ++p) {
-            const Q2Entry e = f.q2[f.part_sorted[p]];
-            if (e.ray) {
-                RayTri R;
-                if (!ray_tri_of(f, e.pair, e.id, R)) continue;
-                const int x0 = max(e.X[0], bx), x1 = min(e.X[1], bx + ts - 1);
-                const int y0 = max(e.Y[0], by), y1 = min(e.Y[1], by + ts - 1);
-                if (x0 > x1 || y0 > y1) continue;
-                const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
-                const float rw = __frcp_rn(__int2float_rn(w));
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    int yy, xx;
-                    divmod_small(i, w, rw, yy, xx);
-                    const int x = x0 + xx, y = y0 + yy;
-                    uint64_t key;
-                    if (ray_key(R, x, y, vw, e.id, key)) tile_min(&tw[(y - by) * ts + (x - bx)], key);
-                }
-                continue;
-            }
+        if (tid < np) {
+            const Q2Entry e = f.q2[f.part_sorted[p0 + tid]];
+            PartRec &P = pr[tid];
+            int x0 = 1, x1 = 0, y0 = 1, y1 = 0;
+            P.ray = (int)e.ray;
             SubTri s;
-            for (int c = 0; c < 3; ++c) { s.X[c] = e.X[c]; s.Y[c] = e.Y[c]; s.iz[c] = e.iz[c]; }
-            s.id = e.id;
-            if (!setup_subtri(s, vw.W, vw.H)) continue;
-            const int x0 = max(s.x0, bx), x1 = min(s.x1, bx + ts - 1);
-            const int y0 = max(s.y0, by), y1 = min(s.y1, by + ts - 1);
-            if (x0 > x1 || y0 > y1) continue;
-            const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
-            const float rw = __frcp_rn(__int2float_rn(w));
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                int yy, xx;
-                divmod_small(i, w, rw, yy, xx);
-                const int x = x0 + xx, y = y0 + yy;
-                uint64_t key;
-                if (pixel_key(s, x, y, key)) tile_min(&tw[(y - by) * ts + (x - bx)], key);
+            if (e.ray) {
+                if (ray_tri_of(f, e.pair, e.id, P.R)) {
+                    x0 = max(e.X[0], bx); x1 = min(e.X[1], bx + ts - 1);
+                    y0 = max(e.Y[0], by); y1 = min(e.Y[1], by + ts - 1);
+                }
+            } else {
+                for (int c = 0; c < 3; ++c) { s.X[c] = e.X[c]; s.Y[c] = e.Y[c]; s.iz[c] = e.iz[c]; }
+                s.id = e.id;
+                if (setup_subtri(s, vw.W, vw.H)) {
+                    x0 = max(s.x0, bx); x1 = min(s.x1, bx + ts - 1);
+                    y0 = max(s.y0, by); y1 = min(s.y1, by + ts - 1);
+                }
             }
+            s.id = e.id;
+            s.x0 = x0 - bx; s.x1 = x1 - bx; s.y0 = y0 - by; s.y1 = y1 - by;   // tile-local, empty if x0 > x1
+            P.s = s;
         }
         __syncthreads();
-        // one global atomic minimum per pixel the tile's parts covered
-        for (int i = threadIdx.x; i < npx; i += blockDim.x) {
-            const uint64_t key = tw[i];
-            if (key != kEmpty) {
-                const int x = bx + (i & (ts - 1)), y = by + (i >> tl);
-                depth_test_write(vw.vis, (size_t)y * (size_t)vw.W + (size_t)x, key);
+        int ux0 = ts, ux1 = -1, uy0 = ts, uy1 = -1;                     // union of the ranges
+        for (int j = 0; j < np; ++j) {
+            const int rx0 = pr[j].s.x0, rx1 = pr[j].s.x1, ry0 = pr[j].s.y0, ry1 = pr[j].s.y1;
+            if (rx0 > rx1 || ry0 > ry1) continue;
+            ux0 = min(ux0, rx0); ux1 = max(ux1, rx1); uy0 = min(uy0, ry0); uy1 = max(uy1, ry1);
+            if (lx < rx0 || lx > rx1) continue;                          // not my column
+            // my first row in range: ly0 + k dyr >= ry0
+            int y = ly0 + (ry0 > ly0 ? ((ry0 - ly0 + dyr - 1) / dyr) * dyr : 0);
+            if (y > ry1) continue;
+            const int x = bx + lx;
+            if (pr[j].ray) {
+                const RayTri R = pr[j].R;
+                const uint64_t id = pr[j].s.id;
+                for (; y <= ry1; y += dyr) {
+                    uint64_t key;
+                    if (ray_key(R, x, by + y, vw, id, key) && key < tw[(y << tl) + lx]) tw[(y << tl) + lx] = key;
+                }
+            } else {
+                const SubTri s = pr[j].s;
+                const int64_t px = 256 * (int64_t)x + 128, py = 256 * (int64_t)(by + y) + 128;
+                // edge k from vertex k+1 to vertex k+2, stepped by dyr rows
+                const int64_t dx0 = (int64_t)(s.X[2] - s.X[1]), dy0 = (int64_t)(s.Y[2] - s.Y[1]);
+                const int64_t dx1 = (int64_t)(s.X[0] - s.X[2]), dy1 = (int64_t)(s.Y[0] - s.Y[2]);
+                const int64_t dx2 = (int64_t)(s.X[1] - s.X[0]), dy2 = (int64_t)(s.Y[1] - s.Y[0]);
+                int64_t E0 = dx0 * (py - s.Y[1]) - dy0 * (px - s.X[1]);
+                int64_t E1 = dx1 * (py - s.Y[2]) - dy1 * (px - s.X[2]);
+                int64_t E2 = dx2 * (py - s.Y[0]) - dy2 * (px - s.X[0]);
+                const int64_t st = 256 * (int64_t)dyr;
+                const int64_t b0 = s.bias & 1u, b1 = (s.bias >> 1) & 1u, b2 = (s.bias >> 2) & 1u;
+                for (; y <= ry1; y += dyr) {
+                    if (((E0 - b0) | (E1 - b1) | (E2 - b2)) >= 0) {
+                        const uint64_t key = frag_key(E0, E1, E2, s.A, s.iz, s.id);
+                        if (key < tw[(y << tl) + lx]) tw[(y << tl) + lx] = key;
+                    }
+                    E0 += dx0 * st; E1 += dx1 * st; E2 += dx2 * st;
+                }
+            }
+        }
+        // one global atomic minimum per covered pixel of mine, resetting the
+        // word (each thread reads and resets only its own pixels; the barrier
+        // at the top of the loop orders pr[] and s_i)
+        if (ux0 <= ux1 && lx >= ux0 && lx <= ux1) {
+            int y = ly0 + (uy0 > ly0 ? ((uy0 - ly0 + dyr - 1) / dyr) * dyr : 0);
+            for (; y <= uy1; y += dyr) {
+                const uint64_t key = tw[(y << tl) + lx];
+                if (key != kEmpty) {
+                    depth_test_write(vw.vis, (size_t)(by + y) * (size_t)vw.W + (size_t)(bx + lx), key);
+                    tw[(y << tl) + lx] = kEmpty;
+                }
             }
         }
         __syncthreads();
@@ -643,18 +678,24 @@ __global__ void k_aabb_final(const float *part, int n, float *out) {
 }
 
 // -------------------------------------------------------------- launchers --
-template <bool INST, bool FUSED, bool COMP>
+template <bool INST, bool FUSED, bool COMP, bool NEAR = true>
 cudaError_t stage1_shape(int *blocks) {
     const size_t sm = stage1_smem_bytes<INST, FUSED>();
-    cudaError_t e = cudaFuncSetAttribute(k_stage1<INST, FUSED, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_stage1<INST, FUSED, COMP, NEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_stage1<INST, FUSED, COMP>, s1::kThreads, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_stage1<INST, FUSED, COMP, NEAR>, s1::kThreads, sm);
 }
 
 cudaError_t query_launch_shape(LaunchShape *o, int device) {
     cudaError_t e = cudaDeviceGetAttribute(&o->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
     if ((e = stage1_shape<false, false, false>(&o->stage1_blocks_per_sm[0][0])) != cudaSuccess) return e;
+    {   // the forms without the near-plane test run at the same shape
+        int b = 0;
+        if ((e = stage1_shape<false, false, false, false>(&b)) != cudaSuccess) return e;
+        if ((e = stage1_shape<false, false, true, false>(&b)) != cudaSuccess) return e;
+    }
     if ((e = stage1_shape<false, true, false>(&o->stage1_blocks_per_sm[0][1])) != cudaSuccess) return e;
     if ((e = stage1_shape<false, false, true>(&o->stage1_blocks_per_sm[0][2])) != cudaSuccess) return e;
     if ((e = stage1_shape<true, false, false>(&o->stage1_blocks_per_sm[1][0])) != cudaSuccess) return e;
@@ -694,7 +735,8 @@ cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32_t r, int blocks, cudaStream_t s) {
+cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32_t r, int blocks, bool near,
+                          cudaStream_t s) {
     const size_t s0 = stage1_smem_bytes<false, false>(), s1f = stage1_smem_bytes<false, true>();
     const size_t i0 = stage1_smem_bytes<true, false>(), i1f = stage1_smem_bytes<true, true>();
     if (instanced) {
@@ -704,8 +746,10 @@ cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32
     } else {
         if (variant == 3) k_stage1_win<<<blocks, s1::kThreads, stage1_win_smem_bytes(), s>>>(f, r);
         else if (variant == 1) k_stage1<false, true, false><<<blocks, s1::kThreads, s1f, s>>>(f, r);
-        else if (variant == 2) k_stage1<false, false, true><<<blocks, s1::kThreads, s0, s>>>(f, r);
-        else k_stage1<false, false, false><<<blocks, s1::kThreads, s0, s>>>(f, r);
+        else if (variant == 2 && near) k_stage1<false, false, true, true><<<blocks, s1::kThreads, s0, s>>>(f, r);
+        else if (variant == 2) k_stage1<false, false, true, false><<<blocks, s1::kThreads, s0, s>>>(f, r);
+        else if (near) k_stage1<false, false, false, true><<<blocks, s1::kThreads, s0, s>>>(f, r);
+        else k_stage1<false, false, false, false><<<blocks, s1::kThreads, s0, s>>>(f, r);
     }
     return cudaGetLastError();
 }

@@ -73,6 +73,10 @@ struct MeshRec {
     uint64_t cwords = 0;
     uint32_t bits = 0, imin = 0;
     float clo[3] = {0, 0, 0}, cstep[3] = {0, 0, 0};
+    // texture (borrowed): per-vertex uv and an RGBA8 mip chain
+    const float *uv = nullptr;
+    const uint8_t *tex = nullptr;
+    int32_t tex_log2 = 0;
 };
 
 struct InstRec {
@@ -155,7 +159,7 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     std::memset(p.fn, 0, sizeof(p.fn));
     std::memset(p.fk, 0, sizeof(p.fk));
     std::memset(p.fs, 0, sizeof(p.fs));
-    p.pad = 0.0f;
+    p.nlo = -INFINITY;
     p.wsafe = INFINITY;
     p.win = 0.0f;
     if (!m.bounded) return;
@@ -175,6 +179,17 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
         p.fn[j] = (float)(ax * (double)p.mv[j] + bx * wr);
         p.fn[4 + j] = (float)(ay * (double)p.mv[4 + j] + by * wr);
         p.fn[8 + j] = (float)wr;
+    }
+    // Near plane: the w row holds the exact path's own coefficients, negated,
+    // so the FMA estimate and the exact path's w (three products and sums
+    // without FMA) are each within 3.01 u S_z of the true value; a vertex
+    // whose estimate lies below near - 8 u S_z is beyond the near plane in
+    // the exact path, and a triangle with all three there is dropped by it.
+    {
+        const double nl = (double)v.nearv - 8 * u * S[2];
+        float f = (float)nl;
+        if ((double)f > nl) f = std::nextafter(f, -INFINITY);
+        p.nlo = f;
     }
     // Error budget per coordinate (pixels), exact path plus estimate:
     //   (9.002u a S_axis + 4.001u b S_z + 4.001u h S_z + 7.002u (|X'| + 1) S_z) / w
@@ -214,6 +229,23 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     p.win = (float)win;
 }
 
+// Whether the near-plane test of the stage-1 cull could fire for a pair: w is
+// affine in the position, so its smallest value over the mesh bounds is at
+// a corner; when that (in double) clears near by 16 u S_z, every vertex's
+// estimated w lies above the pair's nlo and the test never drops anything.
+bool may_reach_near(const PairDev &p, const MeshRec &m, const Cam &cam) {
+    if (!(p.nlo > -INFINITY)) return false;           // the test is off for this pair
+    const double u = std::ldexp(1.0, -24);
+    double S = std::fabs((double)p.mv[11]), wmin = INFINITY;
+    for (int j = 0; j < 3; ++j) S += std::fabs((double)p.mv[8 + j]) * std::max(std::fabs(m.lo[j]), std::fabs(m.hi[j]));
+    for (int k = 0; k < 8; ++k) {
+        double w = -(double)p.mv[11];
+        for (int j = 0; j < 3; ++j) w -= (double)p.mv[8 + j] * ((k >> j) & 1 ? m.hi[j] : m.lo[j]);
+        wmin = std::min(wmin, w);
+    }
+    return !(wmin > (double)cam.nearv + 16 * u * S);
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 curast_config default_config() {
@@ -229,7 +261,7 @@ curast_config default_config() {
     c.stage1_bitmap_bytes = 1ull << 32;
     c.stage1_group_min_pairs = 2;
     c.stage1_vertex_reuse = 0;
-    c.stage3_tile_buffer = 1;
+    c.stage3_tile_buffer = 0;
     c.check_indices = 1;
     c.collect_stats = 0;
     return c;
@@ -266,6 +298,7 @@ struct curast_ctx {
     std::vector<SegDev> hs;
     FrameHdr hdr{};
     bool instanced = false;
+    bool near_needed = true;              // some pair's mesh bounds reach the near plane
 
     DevBuf<Q1Entry> d_q1;
     DevBuf<uint32_t> d_bits;              // survivor bitmap of one stage-1 round
@@ -273,7 +306,8 @@ struct curast_ctx {
     std::vector<char> round_comp;         // the round's meshes are compressed
     DevBuf<Q2Entry> d_q2;
     DevBuf<uint32_t> d_sorted;            // queue-2 indices in tile order (binned stage 3)
-    DevBuf<uint32_t> d_tiles;             // per tile: count | start (+1) | fill | list
+    DevBuf<uint32_t> d_tiles;             // per tile: count | start (+1) | fill
+    DevBuf<uint2> d_units;                // stage-3 units: (tile, first part), up to 8 parts each
     uint32_t n_tiles = 0;
     Counters *d_ctr = nullptr;
     unsigned *d_err = nullptr;
@@ -333,6 +367,9 @@ curast_status sync_scene(curast_ctx *c, cudaStream_t s) {
             md[i].rgba = r.rgba;
             md[i].V = r.V;
             md[i].T = r.T;
+            md[i].uv = r.uv;
+            md[i].tex = r.tex;
+            md[i].tex_log2 = r.tex_log2;
             if (r.comp) {
                 md[i].cidx = r.cidx;
                 md[i].qpos = r.qpos;
@@ -396,6 +433,7 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
     }
     c->hp.clear();
     c->hs.clear();
+    c->near_needed = false;
     const uint64_t per_item = 256ull * c->cfg.stage1_tri_per_thread;
     const size_t m0 = only_mesh < 0 ? 0 : (size_t)only_mesh;
     const size_t m1 = only_mesh < 0 ? c->meshes.size() : (size_t)only_mesh + 1;
@@ -412,7 +450,8 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
                 p.view = (uint32_t)v;
                 p.mesh = (uint32_t)m;
                 fast_constants(p, mr, c->hv[v]);
-                if (c->cfg.stage1_exact_all) p.wsafe = INFINITY;   // the conservative cull never applies
+                if (c->cfg.stage1_exact_all) p.wsafe = INFINITY, p.nlo = -INFINITY;   // no conservative cull
+                c->near_needed = c->near_needed || may_reach_near(p, mr, cams[v]);
                 c->hp.push_back(p);
             }
         }
@@ -500,7 +539,11 @@ curast_status build_frame(curast_ctx *c, const curast_view *views, int nv, long 
         }
         if (nt >= (1ull << 31)) return CURAST_ERR_INVALID_ARG;
         c->n_tiles = (uint32_t)nt;
-        if (c->cfg.stage3_tile_buffer) CU(c->d_tiles.reserve(4 * nt + 1));
+        if (c->cfg.stage3_tile_buffer) {
+            CU(c->d_tiles.reserve(3 * nt + 1));
+            // a tile of c parts makes ceil(c / 8) units
+            CU(c->d_units.reserve(nt + c->cfg.queue2_capacity / 8 + 1));
+        }
     }
     c->hdr.n_batches = nb;
     c->hdr.n_segs = (uint32_t)c->hs.size();
@@ -575,13 +618,14 @@ FrameDev make_frame_dev(const curast_ctx *c) {
     f.stats = c->cfg.collect_stats;
     f.s3_bin = c->cfg.stage3_tile_buffer;
     f.n_tiles = c->n_tiles;
-    f.tile_cnt = f.tile_start = f.tile_fill = f.tile_list = f.part_sorted = nullptr;
+    f.tile_cnt = f.tile_start = f.tile_fill = f.part_sorted = nullptr;
+    f.units = nullptr;
     if (f.s3_bin) {
         f.tile_cnt = c->d_tiles.p;
         f.tile_start = f.tile_cnt + c->n_tiles;
         f.tile_fill = f.tile_start + c->n_tiles + 1;
-        f.tile_list = f.tile_fill + c->n_tiles;
         f.part_sorted = c->d_sorted.p;
+        f.units = c->d_units.p;
     }
     return f;
 }
@@ -602,7 +646,7 @@ curast_status enqueue_stages(curast_ctx *c, bool clear, bool timing, cudaStream_
     for (uint32_t r = 0; r < nr; ++r) {
         const int variant = c->round_comp[r] ? 2 : (!c->instanced && c->cfg.stage1_vertex_reuse ? 3 : 0);
         CU(launch_stage1(f, c->instanced, variant, r, sms * c->shape.stage1_blocks_per_sm[c->instanced ? 1 : 0][variant],
-                         s));
+                         c->near_needed, s));
         if (timing && r + 1 == nr) CU(cudaEventRecord(c->ev[2], s));
         CU(launch_stage1_exact(f, r, sms * c->shape.stage1x_blocks_per_sm, s));
     }
@@ -631,7 +675,8 @@ curast_status render_views(curast_ctx *c, const curast_view *views, int nv, long
     std::vector<uint64_t> key = {(uint64_t)nv, (uint64_t)c->instanced, (uint64_t)clear,
                                  (uint64_t)(uintptr_t)c->d_tab.p, (uint64_t)(uintptr_t)c->d_meshes.p,
                                  (uint64_t)(uintptr_t)c->d_bits.p, (uint64_t)c->rounds.size(),
-                                 (uint64_t)(uintptr_t)c->d_tiles.p, (uint64_t)(uintptr_t)c->d_sorted.p};
+                                 (uint64_t)(uintptr_t)c->d_tiles.p, (uint64_t)(uintptr_t)c->d_sorted.p,
+                                 (uint64_t)(uintptr_t)c->d_units.p};
     for (char rc : c->round_comp) key.push_back((uint64_t)rc);
     for (int v = 0; v < nv; ++v) {
         key.push_back((uint64_t)views[v].W);
@@ -878,6 +923,7 @@ void curast_destroy(curast_ctx *c) {
     c->d_q2.release();
     c->d_sorted.release();
     c->d_tiles.release();
+    c->d_units.release();
     c->d_bits.release();
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->d_err) cudaFree(c->d_err);
@@ -1046,6 +1092,44 @@ curast_status curast_resolve(curast_ctx *c, const float view[16], const float pr
     a.rgba_f32 = rgba_f32;
     a.rgba8 = rgba8;
     CU(launch_resolve(a, s));
+    return CURAST_OK;
+}
+
+curast_status curast_set_mesh_texture(curast_ctx *c, uint32_t mesh_id, const float *uv, const uint8_t *texels,
+                                     int log2_size) {
+    if (!c || mesh_id >= c->meshes.size()) return CURAST_ERR_INVALID_ARG;
+    MeshRec &m = c->meshes[mesh_id];
+    if (!texels) {
+        m.uv = nullptr;
+        m.tex = nullptr;
+        m.tex_log2 = 0;
+    } else {
+        if ((!uv && m.V > 0) || log2_size < 0 || log2_size > 15) return CURAST_ERR_INVALID_ARG;
+        if ((reinterpret_cast<uintptr_t>(uv) & 7) || (reinterpret_cast<uintptr_t>(texels) & 3))
+            return CURAST_ERR_INVALID_ARG;
+        m.uv = uv;
+        m.tex = texels;
+        m.tex_log2 = log2_size;
+    }
+    c->meshes_dirty = true;
+    return CURAST_OK;
+}
+
+curast_status curast_resolve_textured(curast_ctx *c, const float view[16], const float proj[16], int W, int H,
+                                      const uint64_t *vis, float *rgba_f32, uint8_t *rgba8, uint8_t *level,
+                                      curast_stream stream) {
+    if (!c) return CURAST_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(rgba_f32) & 15) || (reinterpret_cast<uintptr_t>(rgba8) & 3))
+        return CURAST_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ShadeArgs a;
+    curast_status st = shade_setup(c, view, proj, W, H, vis, &a, s);
+    if (st != CURAST_OK) return st;
+    a.rgba_f32 = rgba_f32;
+    a.rgba8 = rgba8;
+    a.level = level;
+    CU(launch_resolve_textured(a, s));
     return CURAST_OK;
 }
 

@@ -133,6 +133,82 @@ __global__ void __launch_bounds__(256) k_resolve_ss(ShadeArgs a, int W, int H) {
     store_rgba(a, (size_t)y * W + x, sum);
 }
 
+// ------------------------------------------------------- textured resolve --
+// Section 4.4 "Shading and Mip Mapping": rays through the centres of the
+// pixel and of its right (x + 1), top (y + 1) and top-right neighbours meet
+// the plane of the pixel's triangle; their barycentrics (unclamped: points
+// off the triangle extrapolate) interpolate the vertex uv; the footprint is
+// the larger side of the four samples' uv bounding box in level-0 texels,
+// F = max(du, dv) 2^L, and the level is floor(log2 F) -- read off the
+// float's exponent -- clamped to 0..L (0 when F < 1).  The colour is the
+// nearest texel of that level at the pixel's own uv (column floor(u s), row
+// floor(v s), s the level's side, clamped to it), c = byte / 255.  Pixels of
+// meshes without a texture take the vertex colours of k_resolve.
+__global__ void __launch_bounds__(256) k_resolve_tex(ShadeArgs a) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= a.W || y >= a.H) return;
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int lev = 255;
+    PixelTri pt;
+    MeshDev m;
+    if (lookup(a, a.vis[(size_t)y * a.W + x], pt, m)) {
+        if (m.uv) {
+            const float2 t0 = reinterpret_cast<const float2 *>(m.uv)[pt.vi[0]];
+            const float2 t1 = reinterpret_cast<const float2 *>(m.uv)[pt.vi[1]];
+            const float2 t2 = reinterpret_cast<const float2 *>(m.uv)[pt.vi[2]];
+            float us[4], vs[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float b0, b1, b2;
+                ray_bary(pixel_ray(x + (q & 1), y + (q >> 1), a.W, a.H, a.fx, a.fy), pt.v[0], pt.v[1], pt.v[2], b0,
+                         b1, b2);
+                us[q] = interp3(b0, b1, b2, t0.x, t1.x, t2.x);
+                vs[q] = interp3(b0, b1, b2, t0.y, t1.y, t2.y);
+            }
+            const float du = __fsub_rn(fmaxf(fmaxf(us[0], us[1]), fmaxf(us[2], us[3])),
+                                       fminf(fminf(us[0], us[1]), fminf(us[2], us[3])));
+            const float dv = __fsub_rn(fmaxf(fmaxf(vs[0], vs[1]), fmaxf(vs[2], vs[3])),
+                                       fminf(fminf(vs[0], vs[1]), fminf(vs[2], vs[3])));
+            const int L = m.tex_log2;
+            const float F = __fmul_rn(fmaxf(du, dv), __int2float_rn(1 << L));
+            lev = 0;
+            if (F >= 1.0f) lev = isfinite(F) ? (int)((__float_as_uint(F) >> 23) & 0xFFu) - 127 : L;
+            lev = min(lev, L);
+            // level lev follows the finer levels' sum of (2^(L - l))^2 texels
+            uint64_t off = 0;
+            for (int l = 0; l < lev; ++l) off += 1ull << (2 * (L - l));
+            const int side = 1 << (L - lev);
+            const float fs = __int2float_rn(side);
+            float cu = floorf(__fmul_rn(us[0], fs)), cv = floorf(__fmul_rn(vs[0], fs));
+            if (!(cu >= 0.0f)) cu = 0.0f;
+            if (cu > __fsub_rn(fs, 1.0f)) cu = __fsub_rn(fs, 1.0f);
+            if (!(cv >= 0.0f)) cv = 0.0f;
+            if (cv > __fsub_rn(fs, 1.0f)) cv = __fsub_rn(fs, 1.0f);
+            const uint64_t texel = off + (uint64_t)(uint32_t)cv * (uint64_t)side + (uint64_t)(uint32_t)cu;
+            const uchar4 q = reinterpret_cast<const uchar4 *>(m.tex)[texel];
+            c[0] = __fdiv_rn(__uint2float_rn(q.x), 255.0f);
+            c[1] = __fdiv_rn(__uint2float_rn(q.y), 255.0f);
+            c[2] = __fdiv_rn(__uint2float_rn(q.z), 255.0f);
+            c[3] = __fdiv_rn(__uint2float_rn(q.w), 255.0f);
+        } else if (m.rgba) {
+            float b0, b1, b2;
+            ray_bary(pixel_ray(x, y, a.W, a.H, a.fx, a.fy), pt.v[0], pt.v[1], pt.v[2], b0, b1, b2);
+            const uchar4 q0 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[0]];
+            const uchar4 q1 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[1]];
+            const uchar4 q2 = reinterpret_cast<const uchar4 *>(m.rgba)[pt.vi[2]];
+            const unsigned char s0[4] = {q0.x, q0.y, q0.z, q0.w}, s1[4] = {q1.x, q1.y, q1.z, q1.w},
+                                s2[4] = {q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch)
+                c[ch] = interp3(b0, b1, b2, __fdiv_rn(__uint2float_rn(s0[ch]), 255.0f),
+                                __fdiv_rn(__uint2float_rn(s1[ch]), 255.0f), __fdiv_rn(__uint2float_rn(s2[ch]), 255.0f));
+        }
+    }
+    const size_t pix = (size_t)y * a.W + x;
+    if (a.level) a.level[pix] = (uint8_t)lev;
+    store_rgba(a, pix, c);
+}
+
 // ------------------------------------------------------- interpolate fwd --
 __global__ void __launch_bounds__(256) k_interp_fwd(ShadeArgs a) {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -264,6 +340,11 @@ cudaError_t launch_resolve_ss(const ShadeArgs &a, int W, int H, cudaStream_t s) 
 
 cudaError_t launch_resolve(const ShadeArgs &a, cudaStream_t s) {
     k_resolve<<<pixel_grid(a.W, a.H), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resolve_textured(const ShadeArgs &a, cudaStream_t s) {
+    k_resolve_tex<<<pixel_grid(a.W, a.H), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -69,7 +69,8 @@ struct __align__(16) FastPair {
     float4 k;                   // ka, kb, kc, kd
     float4 lim;                 // wsafe, win, W - 1, H - 1 (every w > wsafe and |X'|, |Y'| < win;
                                 // the last pixel centre)
-    float4 sl;                  // rounding bound of the rows over the mesh bounds (group test), 0
+    float4 sl;                  // rounding bound of the rows over the mesh bounds (group test), and
+                                // nlo: every w below it is beyond the near plane in the exact path
 };
 
 struct Tri9 { float v[9]; };    // the three vertices of a triangle
@@ -83,7 +84,7 @@ struct Tri9 { float v[9]; };    // the three vertices of a triangle
 __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
     // vertex by vertex into running bounds (few live registers); the host
     // chose wsafe so that every w > wsafe keeps the margin m below 1/2
-    float xmn, xmx, ymn, ymx, wmn, rmx;
+    float xmn, xmx, ymn, ymx, wmn, wmx, rmx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float x = p.v[3 * c], y = p.v[3 * c + 1], z = p.v[3 * c + 2];
@@ -94,11 +95,11 @@ __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
         const float r = rcp_approx(w);
         const float X = xw * r, Y = yw * r;
         if (c == 0) {
-            xmn = xmx = X; ymn = ymx = Y; wmn = w; rmx = r;
+            xmn = xmx = X; ymn = ymx = Y; wmn = wmx = w; rmx = r;
         } else {
             xmn = fminf(xmn, X); xmx = fmaxf(xmx, X);
             ymn = fminf(ymn, Y); ymx = fmaxf(ymx, Y);
-            wmn = fminf(wmn, w); rmx = fmaxf(rmx, r);
+            wmn = fminf(wmn, w); wmx = fmaxf(wmx, w); rmx = fmaxf(rmx, r);
         }
     }
     const float4 k = fp.k, lim = fp.lim;
@@ -108,7 +109,8 @@ __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
     // no integer in [lo, hi] within [0, last] on one axis: floor(min(hi, last)) < max(lo, 0)
     const bool nx = floorf(fminf(xmx + m, lim.z)) < fmaxf(xmn - m, 0.0f);
     const bool ny = floorf(fminf(ymx + m, lim.w)) < fmaxf(ymn - m, 0.0f);
-    return safe & (nx | ny);
+    // or every vertex beyond the near plane
+    return (safe & (nx | ny)) | (wmx < fp.sl.w);
 }
 
 // Packed FP32 pairs (Blackwell f32x2): two independent operations in one
@@ -148,9 +150,11 @@ __device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
 
 // fast_cull for two triangles of the same pair at once: the same arithmetic,
 // with the FMA rows, the products by 1/w, the margin and the widened bounds
-// evaluated on packed pairs (one triangle per half).
+// evaluated on packed pairs (one triangle per half).  NEAR = false leaves the
+// near-plane test out (frames where no vertex can lie near that plane).
+template <bool NEAR = true>
 __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, const Tri9 &q, bool &cp, bool &cq) {
-    float2 xmn, xmx, ymn, ymx, wmn, rmx;
+    float2 xmn, xmx, ymn, ymx, wmn, wmx, rmx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float2 x = make_float2(p.v[3 * c], q.v[3 * c]);
@@ -163,13 +167,14 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
         const float2 r = make_float2(rcp_approx(w.x), rcp_approx(w.y));
         const float2 X = mul_x2(xw, r), Y = mul_x2(yw, r);
         if (c == 0) {
-            xmn = xmx = X; ymn = ymx = Y; wmn = w; rmx = r;
+            xmn = xmx = X; ymn = ymx = Y; wmn = wmx = w; rmx = r;
         } else {
             xmn = make_float2(fminf(xmn.x, X.x), fminf(xmn.y, X.y));
             xmx = make_float2(fmaxf(xmx.x, X.x), fmaxf(xmx.y, X.y));
             ymn = make_float2(fminf(ymn.x, Y.x), fminf(ymn.y, Y.y));
             ymx = make_float2(fmaxf(ymx.x, Y.x), fmaxf(ymx.y, Y.y));
             wmn = make_float2(fminf(wmn.x, w.x), fminf(wmn.y, w.y));
+            if (NEAR) wmx = make_float2(fmaxf(wmx.x, w.x), fmaxf(wmx.y, w.y));
             rmx = make_float2(fmaxf(rmx.x, r.x), fmaxf(rmx.y, r.y));
         }
     }
@@ -183,6 +188,10 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
     const bool nyp = floorf(fminf(yh.x, lim.w)) < fmaxf(yl.x, 0.0f), nyq = floorf(fminf(yh.y, lim.w)) < fmaxf(yl.y, 0.0f);
     cp = sp & (nxp | nyp);
     cq = sq & (nxq | nyq);
+    if (NEAR) {                                       // or every vertex beyond the near plane
+        cp |= wmx.x < fp.sl.w;
+        cq |= wmx.y < fp.sl.w;
+    }
 }
 
 // The same test for a whole group of triangles and one pair, from the
@@ -221,7 +230,8 @@ __device__ __forceinline__ bool group_cull(const FastPair &fp, float3 c, float3 
     const bool safe = (wl > lim.x) & (a < lim.y);
     const bool nx = floorf(fminf(X0 + hx + m, lim.z)) < fmaxf(X0 - hx - m, 0.0f);
     const bool ny = floorf(fminf(Y0 + hy + m, lim.w)) < fmaxf(Y0 - hy - m, 0.0f);
-    return safe & (nx | ny);
+    // or the whole box beyond the near plane: w <= w(c) + its weighted extent
+    return (safe & (nx | ny)) | (__fadd_rn(cw, ew) < sl.w);
 }
 
 // The exact path of one (triangle, pair) that the conservative cull kept:
@@ -415,7 +425,7 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
             fp.rw = make_float4(pr.fn[8], pr.fn[9], pr.fn[10], pr.fn[11]);
             fp.k = make_float4(pr.fk[0], pr.fk[1], pr.fk[2], pr.fk[3]);
             fp.lim = make_float4(pr.wsafe, pr.win, (float)(vw.W - 1), (float)(vw.H - 1));
-            fp.sl = make_float4(pr.fs[0], pr.fs[1], pr.fs[2], 0.0f);
+            fp.sl = make_float4(pr.fs[0], pr.fs[1], pr.fs[2], pr.nlo);
             S.fp[slot][q] = fp;
         }
         uint32_t bytes = 12u * d.n;
@@ -453,7 +463,7 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
 // bitmap) queues the survivors per warp and runs the exact path itself,
 // 32 at a time.  INST blocks loop over many pairs (Section 4.5, extended to
 // several views): a triangle's data is loaded once for all of them.
-template <bool INST, bool FUSED, bool COMP>
+template <bool INST, bool FUSED, bool COMP, bool NEAR = true>
 __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullBlocks)
     k_stage1(const __grid_constant__ FrameDev f, uint32_t r) {
     static_assert(!(FUSED && COMP), "the fused kernel reads uncompressed meshes only");
@@ -547,7 +557,7 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
                     for (uint32_t pi = 0; pi < np; ++pi) {
                         bool cull[NT];
                         static_assert(NT == 2, "the cull evaluates triangles in packed pairs");
-                        fast_cull2(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
+                        fast_cull2<NEAR>(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
 #pragma unroll
                         for (int u = 0; u < NT; ++u) {
                             const bool live = valid[u] && !cull[u];
@@ -654,7 +664,7 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
                             const uint32_t pi = (uint32_t)__ffsll((long long)keep) - 1;
                             keep &= keep - 1;
                             bool cull[NT];
-                            fast_cull2(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
+                            fast_cull2<NEAR>(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
 #pragma unroll
                             for (int u = 0; u < NT; ++u) {
                                 const bool live = valid[u] && !cull[u];
@@ -666,7 +676,7 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
                     } else {
                         for (uint32_t pi = 0; pi < np; ++pi) {
                             bool cull[NT];
-                            fast_cull2(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
+                            fast_cull2<NEAR>(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
 #pragma unroll
                             for (int u = 0; u < NT; ++u) {
                                 const bool live = valid[u] && !cull[u];

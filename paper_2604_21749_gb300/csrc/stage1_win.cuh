@@ -275,6 +275,7 @@ __device__ __forceinline__ void win_producer(const FrameDev &f, s1w::Smem &S, co
                 else if (lane == 18) w = (float)(vw.W - 1);
                 else if (lane == 19) w = (float)(vw.H - 1);
                 else if (lane < 23) w = pr.fs[lane - 20];
+                else if (lane == 23) w = pr.nlo;
                 if (lane < kFW) reinterpret_cast<float *>(&S.fp[s])[lane] = w;
                 cur_mesh = d.mesh;
                 cur_pair = d.pair0;

@@ -63,7 +63,7 @@ __global__ void k_static_setup(StaticFrame s) {
         for (int q = 0; q < 12; ++q) p.fn[q] = 0.0f;
         for (int q = 0; q < 4; ++q) p.fk[q] = 0.0f;
         for (int q = 0; q < 3; ++q) p.fs[q] = 0.0f;
-        p.pad = 0.0f;
+        p.nlo = -INFINITY;    // nor a near-plane cull
         p.wsafe = INFINITY;   // no conservative cull: every triangle takes the exact path
         p.win = 0.0f;
         p.base = s.base[t];
@@ -219,14 +219,16 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     f.stats = 0;
     f.s3_bin = 0;     // stage 3 writes straight to the buffer (no tile bins in the scratch)
     f.n_tiles = 0;
-    f.tile_cnt = f.tile_start = f.tile_fill = f.tile_list = f.part_sorted = nullptr;
+    f.tile_cnt = f.tile_start = f.tile_fill = f.part_sorted = nullptr;
+    f.units = nullptr;
 
     const bool inst = n_instances > 1;
     const int sms = ds->shape.num_sms;
     k_static_setup<<<1, 32, 0, s>>>(fr);
     if ((e = cudaGetLastError()) != cudaSuccess) return CURAST_ERR_CUDA;
     if ((e = launch_clear(vis, (uint64_t)W * (uint64_t)H, s)) != cudaSuccess) return CURAST_ERR_CUDA;
-    if ((e = launch_stage1(f, inst, 1, 0, sms * ds->shape.stage1_blocks_per_sm[inst ? 1 : 0][1], s)) != cudaSuccess)
+    if ((e = launch_stage1(f, inst, 1, 0, sms * ds->shape.stage1_blocks_per_sm[inst ? 1 : 0][1], true, s)) !=
+        cudaSuccess)
         return CURAST_ERR_CUDA;
     if ((e = launch_stage2(f, sms * ds->shape.stage2_blocks_per_sm, s)) != cudaSuccess) return CURAST_ERR_CUDA;
     if ((e = launch_stage3(f, sms * ds->shape.stage3_blocks_per_sm, s)) != cudaSuccess) return CURAST_ERR_CUDA;

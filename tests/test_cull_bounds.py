@@ -207,3 +207,48 @@ def test_group_margin_holds_exact_snapped_vertices(setup):
             worst = max(worst, float((exc[ok] / m[ok]).max()))
     assert applied > 0
     assert worst < 1.0, f"an exact snapped vertex lies {worst:.3f} margins outside its group's range"
+
+
+@pytest.mark.parametrize("setup", SETUPS, ids=[s[-1] for s in SETUPS])
+def test_near_plane_bound_holds_exact_depths(setup):
+    """The near-plane cull of stage 1: a vertex whose estimated w (the w row,
+    the exact path's coefficients negated, evaluated by FMA) lies below
+    nlo = near - 8 u S_z has an exact w (the oracle's fixed-order FP32
+    transform) below near, so a triangle with all three vertices there is
+    dropped by the exact path's clipping as well.  Checked on random points
+    of the mesh bounds and on points placed within a few margins of the near
+    plane (solved for the coordinate with the largest w coefficient)."""
+    cam, model, lo, hi, _ = setup
+    cp = orc.camera_params(np.asarray(cam.proj, np.float32))
+    mv = orc.model_view(np.asarray(cam.view, np.float32), model)
+    M = np.asarray(mv, np.float64).reshape(3, 4)
+    amax = np.maximum(np.abs(lo), np.abs(hi))
+    Sz = abs(M[2, 3]) + np.abs(M[2, :3]) @ amax
+    near = float(cp[2])
+    nl = near - 8 * U * Sz
+    nlo = np.float32(nl)
+    if float(nlo) > nl:
+        nlo = np.nextafter(nlo, np.float32(-np.inf))
+    rw = _f32(-M[2])                                   # exact: negation of FP32 coefficients
+    rng = np.random.default_rng(17)
+    pts = rng.uniform(lo, hi, size=(40000, 3))
+    # points on the near plane: w = -(m . p + m3) = near (1 + t), solved for the axis j
+    j = int(np.argmax(np.abs(M[2, :3]) * (hi - lo)))
+    span = max(1e-5, 3 * 8 * U * Sz / near)          # a few times the margin, relative to near
+    t = rng.uniform(-span, span, size=40000)
+    q = rng.uniform(lo, hi, size=(40000, 3))
+    rest = M[2, 3] + sum(M[2, a] * q[:, a] for a in range(3) if a != j)
+    if abs(M[2, j]) > 0:
+        q[:, j] = (-near * (1 + t) - rest) / M[2, j]
+    q = q[((q >= lo) & (q <= hi)).all(1)]
+    pts = np.concatenate([pts, q]).astype(F32)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    w_est = _row(rw, x, y, z)
+    clipv, _, _, _ = orc.project(mv, cp, cam.W, cam.H, pts)
+    w_exact = clipv[:, 2]
+    below = w_est < nlo
+    assert (w_exact[below] < np.float32(near)).all()
+    if len(q) > 100:
+        # the boundary is exercised: points within 1e-5 of the plane on both sides of nlo
+        close = np.abs(w_exact.astype(np.float64) - near) < 2 * span * near
+        assert (below & close).any() and (~below & close).any()

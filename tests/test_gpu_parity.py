@@ -63,7 +63,7 @@ def test_small_workload_bit_exact_and_resolve(api, small):
     dict(stage1_bitmap_bytes=1 << 12), dict(stage1_bitmap_bytes=1 << 12, stage1_tri_per_thread=1),
     dict(stage1_exact_all=1), dict(stage1_exact_all=1, stage1_bitmap_bytes=1 << 12),
     dict(stage1_vertex_reuse=1), dict(stage1_vertex_reuse=1, stage1_tri_per_thread=3),
-    dict(stage3_tile_buffer=0), dict(stage3_tile_buffer=0, tile_log2=4),
+    dict(stage3_tile_buffer=1), dict(stage3_tile_buffer=1, tile_log2=4), dict(stage3_tile_buffer=1, tile_log2=7),
 ])
 def test_stage_choices_never_change_visibility(api, small, cfg):
     """Thresholds, tile size, batch shape and queue overflow move triangles

@@ -34,7 +34,9 @@ def _paper(scene, cam, s1=128, s2=4096):
 
 
 @pytest.mark.parametrize("cfg", [dict(), dict(stage2_max_pixels=32), dict(stage1_max_pixels=16, stage2_max_pixels=64),
-                                 dict(stage2_max_pixels=100000), dict(tile_log2=4)])
+                                 dict(stage2_max_pixels=100000), dict(tile_log2=4),
+                                 dict(stage2_max_pixels=32, stage3_tile_buffer=1),
+                                 dict(tile_log2=5, stage3_tile_buffer=1)])
 def test_small_workload_ray_cast_equals_oracle(api, cfg):
     """The heightfield plus two ground triangles crossing the near plane;
     thresholds moved so that few, many or no triangles are ray cast."""
@@ -74,7 +76,8 @@ def test_room_around_the_camera(api):
     stage 2 and, being huge, the ray cast; with queue capacities of 1 the
     overflow paths ray cast in place."""
     sc = S.scene_room()
-    for cfg in (dict(), dict(queue1_capacity=1, queue2_capacity=1)):
+    for cfg in (dict(), dict(queue1_capacity=1, queue2_capacity=1), dict(stage3_tile_buffer=1),
+                dict(stage3_tile_buffer=1, queue2_capacity=7)):
         r = _renderer(api, **cfg)
         keep = upload(r, sc)
         for cam in sc.cameras:
