@@ -722,10 +722,10 @@ def raycast_stage3(args, dev):
     the paper's ray-cast stage 3 (stage3_raycast): the camera inside a closed
     box at the frame size (every face huge and crossing the near plane), and
     a close-up pose of a 1448^2 heightfield with stage2_max_pixels = 32 so
-    that its large triangles are ray cast.  Each with the shared-memory tile
-    buffer of stage 3 (default) and with every covered pixel written to the
-    global buffer (stage3_tile_buffer = 0, keys *_global_writes).  Frame ms
-    and per-stage ms of each."""
+    that its large triangles are ray cast.  Each with every covered pixel
+    written to the global buffer (the default) and with the shared-memory
+    tile buffer of stage 3 (stage3_tile_buffer = 1, keys *_tile_buffer).
+    Frame ms and per-stage ms of each."""
     import numpy as np
     import torch
     import synthetic as S
@@ -747,7 +747,7 @@ def raycast_stage3(args, dev):
             r.add_instance(it.mesh, it.model)
         vis = r.new_vis(cam.W, cam.H)
         row = {"workload": name}
-        for mode, tb in ((0, 1), (1, 1), (0, 0), (1, 0)):
+        for mode, tb in ((0, 0), (1, 0), (0, 1), (1, 1)):
             r.set_config(stage3_raycast=mode, stage3_tile_buffer=tb, **cfg)
             for _ in range(3):
                 r.render(cam.view, cam.proj, cam.W, cam.H, vis)
@@ -761,7 +761,7 @@ def raycast_stage3(args, dev):
             torch.cuda.synchronize()
             r.render(cam.view, cam.proj, cam.W, cam.H, vis)
             st = r.stage_times()
-            key = ("ray_cast" if mode else "fixed_point") + ("" if tb else "_global_writes")
+            key = ("ray_cast" if mode else "fixed_point") + ("_tile_buffer" if tb else "")
             row[key + "_ms"] = round(e0.elapsed_time(e1) / frames, 4)
             row[key + "_stage_ms"] = {k: round(v, 4) for k, v in
                                       zip(["clear", "stage1_cull", "stage1_exact", "stage2", "stage3"], st)}

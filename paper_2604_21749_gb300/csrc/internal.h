@@ -21,8 +21,8 @@ cudaError_t query_launch_shape(LaunchShape *out, int device);
 cudaError_t launch_clear(uint64_t *vis, uint64_t n, cudaStream_t s);
 // Stage 1 of round r: the cull kernel (fused: it runs the exact path itself
 // and needs no bitmap), then the exact kernel over the round's bitmap.
-// near = false launches the single-pair cull without its near-plane test
-// (valid when no pair's mesh bounds reach the near plane).
+// near = false launches the cull (not the fused form) without its near-plane
+// test (valid when no pair's mesh bounds reach the near plane).
 cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32_t r, int blocks, bool near,
                           cudaStream_t s);
 cudaError_t launch_stage1_exact(const FrameDev &f, uint32_t r, int blocks, cudaStream_t s);

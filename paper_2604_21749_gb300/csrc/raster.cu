@@ -695,6 +695,8 @@ cudaError_t query_launch_shape(LaunchShape *o, int device) {
         int b = 0;
         if ((e = stage1_shape<false, false, false, false>(&b)) != cudaSuccess) return e;
         if ((e = stage1_shape<false, false, true, false>(&b)) != cudaSuccess) return e;
+        if ((e = stage1_shape<true, false, false, false>(&b)) != cudaSuccess) return e;
+        if ((e = stage1_shape<true, false, true, false>(&b)) != cudaSuccess) return e;
     }
     if ((e = stage1_shape<false, true, false>(&o->stage1_blocks_per_sm[0][1])) != cudaSuccess) return e;
     if ((e = stage1_shape<false, false, true>(&o->stage1_blocks_per_sm[0][2])) != cudaSuccess) return e;
@@ -711,6 +713,7 @@ cudaError_t query_launch_shape(LaunchShape *o, int device) {
     }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage1x_blocks_per_sm, k_stage1_exact<false>,
                                                       32 * s1::kExactWarps, 0);
+
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->stage2_blocks_per_sm, k_stage2, 256, 0);
     if (e != cudaSuccess) return e;
@@ -741,8 +744,10 @@ cudaError_t launch_stage1(const FrameDev &f, bool instanced, int variant, uint32
     const size_t i0 = stage1_smem_bytes<true, false>(), i1f = stage1_smem_bytes<true, true>();
     if (instanced) {
         if (variant == 1) k_stage1<true, true, false><<<blocks, s1::kThreads, i1f, s>>>(f, r);
-        else if (variant == 2) k_stage1<true, false, true><<<blocks, s1::kThreads, i0, s>>>(f, r);
-        else k_stage1<true, false, false><<<blocks, s1::kThreads, i0, s>>>(f, r);
+        else if (variant == 2 && near) k_stage1<true, false, true, true><<<blocks, s1::kThreads, i0, s>>>(f, r);
+        else if (variant == 2) k_stage1<true, false, true, false><<<blocks, s1::kThreads, i0, s>>>(f, r);
+        else if (near) k_stage1<true, false, false, true><<<blocks, s1::kThreads, i0, s>>>(f, r);
+        else k_stage1<true, false, false, false><<<blocks, s1::kThreads, i0, s>>>(f, r);
     } else {
         if (variant == 3) k_stage1_win<<<blocks, s1::kThreads, stage1_win_smem_bytes(), s>>>(f, r);
         else if (variant == 1) k_stage1<false, true, false><<<blocks, s1::kThreads, s1f, s>>>(f, r);

@@ -205,6 +205,7 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
 // exact snapped vertices each take their error at the group's largest 1/w
 // and |X'|) holds every exact snapped vertex.  When the widened ranges hold
 // no pixel centre, no triangle's bbox does.
+template <bool NEAR = true>
 __device__ __forceinline__ bool group_cull(const FastPair &fp, float3 c, float3 e) {
     const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw, sl = fp.sl;
     const float cx = __fmaf_rn(rx.x, c.x, __fmaf_rn(rx.y, c.y, __fmaf_rn(rx.z, c.z, rx.w)));
@@ -231,7 +232,7 @@ __device__ __forceinline__ bool group_cull(const FastPair &fp, float3 c, float3 
     const bool nx = floorf(fminf(X0 + hx + m, lim.z)) < fmaxf(X0 - hx - m, 0.0f);
     const bool ny = floorf(fminf(Y0 + hy + m, lim.w)) < fmaxf(Y0 - hy - m, 0.0f);
     // or the whole box beyond the near plane: w <= w(c) + its weighted extent
-    return (safe & (nx | ny)) | (__fadd_rn(cw, ew) < sl.w);
+    return (safe & (nx | ny)) | (NEAR && __fadd_rn(cw, ew) < sl.w);
 }
 
 // The exact path of one (triangle, pair) that the conservative cull kept:
@@ -648,7 +649,7 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
                         uint64_t keep = 0;                 // pairs whose group test failed
                         for (uint32_t pb = 0; pb < np; pb += 32) {
                             const uint32_t q = pb + lane;
-                            const bool g = q < np && group_cull(S.fp[slot][q < np ? q : 0], gc, ge);
+                            const bool g = q < np && group_cull<NEAR>(S.fp[slot][q < np ? q : 0], gc, ge);
                             keep |= (uint64_t)__ballot_sync(0xffffffffu, q < np && !g) << pb;
                         }
                         for (uint32_t i0 = 0; i0 < 2 * np; i0 += 32) {
