@@ -182,12 +182,20 @@ static orc_cv intersect(orc_cv in, orc_cv out, float fin, float fout, int p, flo
 
 /* Sutherland-Hodgman against near, left, right, bottom, top, in that order.
  * Returns the vertex count (0 or 3..8); a triangle inside every plane comes
- * back unchanged and in its own vertex order. */
+ * back unchanged and in its own vertex order -- every pass would keep its
+ * three vertices and cut nothing, so such a triangle is returned at once. */
 int orc_clip(const float tri[9], float nearv, float out[24])
 {
     orc_cv a[9], b[9];
     int n = 3;
     for (int k = 0; k < 3; ++k) { a[k].x = tri[3 * k]; a[k].y = tri[3 * k + 1]; a[k].w = tri[3 * k + 2]; }
+    int inside = 1;
+    for (int k = 0; k < 3; ++k)
+        for (int p = 0; p < 5; ++p) inside = inside && plane_value(p, a[k], nearv) >= 0.0f;
+    if (inside) {
+        memcpy(out, tri, sizeof(float) * 9);
+        return 3;
+    }
     for (int p = 0; p < 5 && n > 0; ++p) {
         int m = 0;
         orc_cv prev = a[n - 1];
