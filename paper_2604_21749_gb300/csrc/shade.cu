@@ -232,31 +232,53 @@ __global__ void __launch_bounds__(256) k_interp_fwd(ShadeArgs a) {
 // Sums `val` over the lanes of the warp holding the same key and adds the
 // sum once per group as an FP32 atomicAdd (warp-aggregated atomics).  All
 // 32 lanes must call it; key 0xFFFFFFFF marks lanes with nothing to add.
-__device__ __forceinline__ void aggregated_add(unsigned key, float *addr, double val) {
+__device__ __forceinline__ void aggregated_add(unsigned key, float *addr, float val) {
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(peers) - 1;
-    double sum = val;
+    float sum = val;
     if (__popc(peers) > 1) {
-        sum = 0.0;
+        sum = 0.0f;
         unsigned m = peers;
         while (m) {
             const int j = __ffs(m) - 1;
             m &= m - 1;
-            sum += __shfl_sync(peers, val, j);
+            sum = __fadd_rn(sum, __shfl_sync(peers, val, j));
         }
     }
-    if (lane == leader && key != 0xffffffffu) atomicAdd(addr, (float)sum);
+    if (lane == leader && key != 0xffffffffu) atomicAdd(addr, sum);
 }
 
 constexpr int kMaxC = 16;
 
-struct D3 { double x, y, z; };
-__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
-    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+// Double-float numbers (hi + lo, |lo| <= ulp(hi) / 2) for the two
+// quantities whose cancellation the backward cannot afford: the view-space
+// vertex v0 and the pixel ray r.  Error-free product by FMA, error-free sum
+// (Knuth's two-sum), and a sum of two double-floats.
+struct DF { float hi, lo; };
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
 }
-__device__ __forceinline__ double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    const DF s = two_sum(x.hi, y.hi);
+    const float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    const float hi = __fadd_rn(s.hi, lo);
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+// a b - c d for double-floats: the hi products error-free, their difference
+// as a double-float, the cross terms in FP32 (they are ulp-sized).
+__device__ __forceinline__ float df_cross1(DF a, DF b, DF c, DF d) {
+    const DF p = two_prod(a.hi, b.hi), q = two_prod(c.hi, d.hi);
+    const DF t = df_add(p, {-q.hi, -q.lo});
+    const float x = __fsub_rn(__fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi)),
+                              __fadd_rn(__fmul_rn(c.hi, d.lo), __fmul_rn(c.lo, d.hi)));
+    return __fadd_rn(t.hi, __fadd_rn(t.lo, x));
+}
 
 // Gradient of I = sum_k b_k c_k with the visibility held fixed.  With
 // D_k = r . (v_{k+1} x v_{k+2}) and S = sum_k D_k the barycentrics are
@@ -264,9 +286,17 @@ __device__ __forceinline__ double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.
 //   dL/dc_k = g b_k,
 //   dL/dv_j = [ (gamma_{j-1} - gbar) (v_{j+1} x r) + (gamma_{j+1} - gbar) (r x v_{j-1}) ] / S,
 //   dL/dp_j = M^T dL/dv_j   (M = the 3x3 part of the instance's model-view).
-// A pixel's hit point lies ~100x closer to its triangle's vertices than the
-// vertices lie to the camera, so the per-pixel geometry is evaluated in FP64
-// (from the FP32 positions and model-view); the scatter stays FP32.
+// A pixel's ray passes ~100x closer to its triangle than the triangle lies
+// to the camera, so written naively these cancel in FP32.  Everything is
+// expressed instead through the ray's moment about v0, m = v0 x r, and the
+// edges E_1 = e1 = v1 - v0, E_2 = e2 = v2 - v0 (E_0 = 0):
+//   D_1 = e2 . m,  D_2 = -(e1 . m),  S = r . (e1 x e2),  D_0 = S - D_1 - D_2,
+//   v_{j+1} x r = m + E_{j+1} x r,  r x v_{j-1} = -(m + E_{j-1} x r),
+// which are all well conditioned once m is: m alone carries the
+// cancellation, and is computed from v0 and r held as double-floats (v0 from
+// the FP32 model-view and position with error-free products, r from FP64)
+// with a compensated cross product.  The edges come from the model-space
+// differences rotated by M.  Everything else is plain FP32.
 __global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
     const bool inside = x < a.W && y < a.H;
@@ -278,46 +308,68 @@ __global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
         pix = (size_t)y * a.W + x;
         hit = lookup(a, a.vis[pix], pt, m) && a.inst_mesh[pt.inst] == a.mesh;
     }
-    double b[3] = {0.0, 0.0, 0.0};
-    double dv[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
-    double g[kMaxC];
-    for (int ch = 0; ch < a.C; ++ch) g[ch] = 0.0;
+    float b[3] = {0.0f, 0.0f, 0.0f};
+    float dv[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+    float g[kMaxC];
+    for (int ch = 0; ch < a.C; ++ch) g[ch] = 0.0f;
     if (hit) {
         const float *mv = a.inst_mv + 12 * (size_t)pt.inst;
         const float *pos = (a.pos && a.inst_mesh[pt.inst] == a.mesh) ? a.pos : m.pos;
-        D3 v[3];
-        for (int k = 0; k < 3; ++k) {
-            const float *p = pos + 3 * (size_t)pt.vi[k];
-            double c[3];
-            for (int r = 0; r < 3; ++r)
-                c[r] = (double)mv[4 * r] * p[0] + (double)mv[4 * r + 1] * p[1] + (double)mv[4 * r + 2] * p[2] +
-                       (double)mv[4 * r + 3];
-            v[k] = {c[0], c[1], c[2]};
+        const float *p0 = pos + 3 * (size_t)pt.vi[0];
+        const float *p1 = pos + 3 * (size_t)pt.vi[1];
+        const float *p2 = pos + 3 * (size_t)pt.vi[2];
+        // v0 as double-floats, row by row
+        DF v0[3];
+        for (int r = 0; r < 3; ++r) {
+            DF acc = two_prod(mv[4 * r], p0[0]);
+            acc = df_add(acc, two_prod(mv[4 * r + 1], p0[1]));
+            acc = df_add(acc, two_prod(mv[4 * r + 2], p0[2]));
+            v0[r] = df_add(acc, {mv[4 * r + 3], 0.0f});
         }
-        const D3 r = {((2.0 * x + 1.0) / a.W - 1.0) / a.fx, ((2.0 * y + 1.0) / a.H - 1.0) / a.fy, -1.0};
-        const D3 e1 = dsub(v[1], v[0]), e2 = dsub(v[2], v[0]);
-        const double S = ddot(r, dcross(e1, e2));
-        double D[3];
-        D[1] = ddot(r, dcross(e2, v[0]));
-        D[2] = ddot(r, dcross(v[0], e1));
-        D[0] = S - D[1] - D[2];
-        const double invS = 1.0 / S;
-        for (int k = 0; k < 3; ++k) b[k] = D[k] * invS;
+        // the pixel-centre ray in FP64, split into double-floats
+        const double rxd = ((2.0 * x + 1.0) / a.W - 1.0) / a.fx, ryd = ((2.0 * y + 1.0) / a.H - 1.0) / a.fy;
+        const DF rx = {(float)rxd, (float)(rxd - (double)(float)rxd)};
+        const DF ry = {(float)ryd, (float)(ryd - (double)(float)ryd)};
+        const DF rz = {-1.0f, 0.0f};
+        const float3 r = make_float3(rx.hi, ry.hi, -1.0f);
+        // m = v0 x r
+        const float3 mm = make_float3(df_cross1(v0[1], rz, v0[2], ry), df_cross1(v0[2], rx, v0[0], rz),
+                                      df_cross1(v0[0], ry, v0[1], rx));
+        // edges: model-space differences through M
+        float3 E[3];
+        E[0] = make_float3(0.0f, 0.0f, 0.0f);
+        for (int k = 1; k < 3; ++k) {
+            const float *pk = k == 1 ? p1 : p2;
+            const float d0 = __fsub_rn(pk[0], p0[0]), d1 = __fsub_rn(pk[1], p0[1]), d2 = __fsub_rn(pk[2], p0[2]);
+            E[k] = make_float3(__fadd_rn(__fadd_rn(__fmul_rn(mv[0], d0), __fmul_rn(mv[1], d1)), __fmul_rn(mv[2], d2)),
+                               __fadd_rn(__fadd_rn(__fmul_rn(mv[4], d0), __fmul_rn(mv[5], d1)), __fmul_rn(mv[6], d2)),
+                               __fadd_rn(__fadd_rn(__fmul_rn(mv[8], d0), __fmul_rn(mv[9], d1)), __fmul_rn(mv[10], d2)));
+        }
+        const float S = dot3(r, cross3(E[1], E[2]));
+        float D[3];
+        D[1] = dot3(E[2], mm);
+        D[2] = -dot3(E[1], mm);
+        D[0] = __fsub_rn(__fsub_rn(S, D[1]), D[2]);
+        const float invS = __frcp_rn(S);
+        for (int k = 0; k < 3; ++k) b[k] = __fmul_rn(D[k], invS);
         for (int ch = 0; ch < a.C; ++ch) g[ch] = a.grad_out[(size_t)a.C * pix + ch];
-        double gam[3];
+        float gam[3];
         for (int k = 0; k < 3; ++k) {
-            double s = 0.0;
-            for (int ch = 0; ch < a.C; ++ch) s += g[ch] * a.attr[(size_t)a.C * pt.vi[k] + ch];
+            float s = 0.0f;
+            for (int ch = 0; ch < a.C; ++ch) s = __fmaf_rn(g[ch], a.attr[(size_t)a.C * pt.vi[k] + ch], s);
             gam[k] = s;
         }
-        const double gbar = b[0] * gam[0] + b[1] * gam[1] + b[2] * gam[2];
+        const float gbar = __fmaf_rn(b[0], gam[0], __fmaf_rn(b[1], gam[1], __fmul_rn(b[2], gam[2])));
         for (int j = 0; j < 3; ++j) {
             const int jm = (j + 2) % 3, jp = (j + 1) % 3;
-            const D3 c1 = dcross(v[jp], r), c2 = dcross(r, v[jm]);
-            const double w1 = (gam[jm] - gbar) * invS, w2 = (gam[jp] - gbar) * invS;
-            const D3 d = {w1 * c1.x + w2 * c2.x, w1 * c1.y + w2 * c2.y, w1 * c1.z + w2 * c2.z};
+            const float w1 = __fmul_rn(__fsub_rn(gam[jm], gbar), invS), w2 = __fmul_rn(__fsub_rn(gam[jp], gbar), invS);
+            const float3 cp = cross3(E[jp], r), cm = cross3(E[jm], r);
+            const float wd = __fsub_rn(w1, w2);
+            const float3 d = make_float3(__fmaf_rn(wd, mm.x, __fsub_rn(__fmul_rn(w1, cp.x), __fmul_rn(w2, cm.x))),
+                                         __fmaf_rn(wd, mm.y, __fsub_rn(__fmul_rn(w1, cp.y), __fmul_rn(w2, cm.y))),
+                                         __fmaf_rn(wd, mm.z, __fsub_rn(__fmul_rn(w1, cp.z), __fmul_rn(w2, cm.z))));
             for (int ax = 0; ax < 3; ++ax)
-                dv[j][ax] = (double)mv[ax] * d.x + (double)mv[4 + ax] * d.y + (double)mv[8 + ax] * d.z;
+                dv[j][ax] = __fmaf_rn(mv[ax], d.x, __fmaf_rn(mv[4 + ax], d.y, __fmul_rn(mv[8 + ax], d.z)));
         }
     }
     for (int j = 0; j < 3; ++j) {
@@ -326,7 +378,8 @@ __global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
         if (a.grad_pos)
             for (int ax = 0; ax < 3; ++ax) aggregated_add(key, a.grad_pos + 3 * vj + ax, dv[j][ax]);
         if (a.grad_attr)
-            for (int ch = 0; ch < a.C; ++ch) aggregated_add(key, a.grad_attr + (size_t)a.C * vj + ch, g[ch] * b[j]);
+            for (int ch = 0; ch < a.C; ++ch)
+                aggregated_add(key, a.grad_attr + (size_t)a.C * vj + ch, __fmul_rn(g[ch], b[j]));
     }
 }
 

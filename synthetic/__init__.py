@@ -11,5 +11,5 @@ from .scenes import (  # noqa: F401
     look_at, perspective,
     scene_small, scene_unique, camera_unique_pose, scene_billion, camera_billion,
     scene_batched, scene_differentiable, target_colour_noise, scene_room,
-    grid_uv, texture_mip_chain,
+    grid_uv, texture_mip_chain, batched_mesh_specs, batched_mesh,
 )

@@ -363,21 +363,41 @@ def scene_billion(device="cpu", tiles: int = 8, n: int = 4096, colours: bool = T
     return Scene(meshes, inst, [])
 
 
-def scene_batched(device="cpu", n_meshes: int = 256, n_instances: int = 10000,
-                  tmin: float = 1e4, tmax: float = 2e7, area: float = 200.0,
-                  views=((3840, 2160), (3840, 2160), (1920, 1080), (1920, 1080)),
-                  seed: int = 300) -> Scene:
-    """Many meshes of log-uniform size, many rigid+uniform-scale instances, several views."""
+def batched_mesh_specs(n_meshes: int = 256, tmin: float = 1e4, tmax: float = 2e7, seed: int = 300) -> list:
+    """The meshes of the many-mesh workload without building them: per mesh
+    (kind, n, seed, T) -- even ones heightfields of n x n cells (T = 2 n^2),
+    odd ones spheres of n x 2n cells (T = 4 n^2) -- with T drawn
+    log-uniform in [tmin, tmax]."""
     rng = np.random.default_rng(seed)
     tcount = np.exp(rng.uniform(math.log(tmin), math.log(tmax), size=n_meshes))
-    meshes = []
+    out = []
     for m in range(n_meshes):
         if m % 2 == 0:
             n = max(2, int(round(math.sqrt(tcount[m] / 2.0))))
-            meshes.append(heightfield_mesh(n, seed=seed + 1 + m, device=device))
+            out.append(("heightfield", n, seed + 1 + m, 2 * n * n))
         else:
             n = max(2, int(round(math.sqrt(tcount[m] / 4.0))))
-            meshes.append(sphere_mesh(n, seed=seed + 1 + m, device=device))
+            out.append(("sphere", n, seed + 1 + m, 4 * n * n))
+    return out
+
+
+def batched_mesh(spec, device="cpu") -> Mesh:
+    kind, n, mseed, _ = spec
+    return heightfield_mesh(n, seed=mseed, device=device) if kind == "heightfield" else \
+        sphere_mesh(n, seed=mseed, device=device)
+
+
+def scene_batched(device="cpu", n_meshes: int = 256, n_instances: int = 10000,
+                  tmin: float = 1e4, tmax: float = 2e7, area: float = 200.0,
+                  views=((3840, 2160), (3840, 2160), (1920, 1080), (1920, 1080)),
+                  seed: int = 300, only=None) -> Scene:
+    """Many meshes of log-uniform size, many rigid+uniform-scale instances,
+    several views.  ``only`` restricts which meshes are built (the others are
+    None placeholders; their triangle counts come from batched_mesh_specs)."""
+    rng = np.random.default_rng(seed)
+    rng.uniform(size=n_meshes)                       # the triangle counts (batched_mesh_specs)
+    specs = batched_mesh_specs(n_meshes, tmin, tmax, seed)
+    meshes = [batched_mesh(sp, device) if only is None or m in only else None for m, sp in enumerate(specs)]
     inst = []
     for k in range(n_instances):
         mesh = k if k < n_meshes else int(rng.integers(0, n_meshes))

@@ -50,3 +50,21 @@ def unique_pose(path_pos, path_idx, k, W, H):
     sc = Scene([m], [Instance(0, np.eye(4, dtype=np.float32))])
     cam = S.camera_unique_pose(k, W, H)
     return O.render(O.OracleScene(sc), cam)
+
+
+def batched_meshes(mesh_ids):
+    """The many-mesh workload's instances of the given meshes rendered into
+    every view (ids numbered over all instances, as in the full scene); the
+    meshes are built here on the CPU.  Returns one buffer per view."""
+    import synthetic as S
+    from oracle import oracle as O
+    specs = S.batched_mesh_specs()
+    sc = S.scene_batched(device="cpu", only=set(mesh_ids))
+    osc = O.OracleScene(sc, tri_counts=[sp[3] for sp in specs])
+    cams = [c for c in sc.cameras]
+    out = [np.full((c.H, c.W), O.EMPTY, np.uint64) for c in cams]
+    for i, it in enumerate(sc.instances):
+        if it.mesh in mesh_ids:
+            for c, buf in zip(cams, out):
+                O.render(osc, c, first=i, count=1, out=buf)
+    return out

@@ -5,9 +5,9 @@ times (default configuration, curast_render / curast_render_batch):
   the whole frame against the oracle, tile by tile in a process pool;
 - the 100M-triangle heightfield, 8 poses at 1920x1080 and 3840x2160;
 - the many-mesh batched workload (256 meshes, 10,000 instances, 4 views):
-  batched (graph) == one launch per mesh per view, every sampled winning
-  fragment re-derived by the oracle, and the same structure at reduced
-  size against the oracle in full;
+  batched (graph) against the oracle in full, every pixel of every view;
+  batched == one launch per mesh per view; and the same structure at
+  reduced size;
 - the differentiable workload (1448^2 cells, 1024^2): forward against the
   FP32 oracle, backward against the FP64 adjoint and central differences.
 
@@ -164,6 +164,52 @@ def test_batched_full_size_equals_per_mesh_launches(api):
             assert ref[y, x] != O.EMPTY, "the winning triangle does not cover its pixel"
             assert (ref[y, x] >> np.uint64(36)) == (key >> np.uint64(36)), "depth of the winner differs"
     r.close()
+
+
+def test_batched_full_size_equals_oracle(api, workers):
+    """The many-mesh workload at full size (256 meshes, 10,000 instances, 4
+    views, about 9.8e10 triangle-instance-views) rendered by the batched
+    launch replayed from its CUDA graph, against the oracle in full: every
+    pixel of every view.  The oracle runs in a process pool, each process
+    building its share of the meshes on the CPU and rendering all of their
+    instances; the shares' buffers merge by an element-wise minimum, which
+    is exact because a visibility word is the minimum over all fragments.
+    Heightfields are built on the GPU (bit-identical to the CPU build);
+    spheres, whose sin/cos may round differently there, are built on the
+    CPU and uploaded."""
+    specs = S.batched_mesh_specs()
+    cams = S.scene_batched(device="cpu", only=set()).cameras
+    # shares of about equal work: meshes by triangles x instances, largest first
+    inst = np.bincount([it.mesh for it in S.scene_batched(device="cpu", only=set()).instances], minlength=len(specs))
+    work = [(sp[3] * int(inst[m]), m) for m, sp in enumerate(specs)]
+    nshare = max(1, min(64, (os.cpu_count() or 2) * 2))
+    shares = [[] for _ in range(nshare)]
+    load = [0] * nshare
+    for w, m in sorted(work, reverse=True):
+        k = int(np.argmin(load))
+        shares[k].append(m)
+        load[k] += w
+    jobs = [workers.apply_async(J.batched_meshes, (sh,)) for sh in shares if sh]
+    sc = S.scene_batched(device="cuda", only={m for m, sp in enumerate(specs) if sp[0] == "heightfield"})
+    for m, sp in enumerate(specs):
+        if sp[0] == "sphere":
+            cpu = S.batched_mesh(sp)
+            sc.meshes[m] = S.Mesh(pos=cpu.pos.cuda(), idx=cpu.idx.cuda(), rgba8=cpu.rgba8.cuda(), aabb=cpu.aabb)
+    r = _batched_renderer(api, sc)
+    out = r.render_batch([(c.view, c.proj, c.W, c.H, None) for c in sc.cameras], use_graph=True)
+    out = r.render_batch([(c.view, c.proj, c.W, c.H, o) for c, o in zip(sc.cameras, out)], use_graph=True)
+    r.sync()
+    got = [u64(v) for v in out]
+    r.close()
+    del sc, out
+    torch.cuda.empty_cache()
+    ref = None
+    for j in jobs:
+        part = j.get(timeout=3000)
+        ref = part if ref is None else [np.minimum(a, b) for a, b in zip(ref, part)]
+    for c, g, w in zip(cams, got, ref):
+        assert (w != O.EMPTY).sum() > 0.5 * c.W * c.H
+        assert_vis_equal(g, w, f"batched full size {c.W}x{c.H}")
 
 
 def test_batched_reduced_equals_oracle(api):
