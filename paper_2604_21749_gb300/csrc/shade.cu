@@ -270,6 +270,22 @@ __device__ __forceinline__ DF df_add(DF x, DF y) {
     const float hi = __fadd_rn(s.hi, lo);
     return {hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
 }
+// x / d for a double-float x and a float d, as a double-float: the first
+// quotient rounded, its remainder exact by FMA, the remainder's quotient.
+__device__ __forceinline__ DF df_div(DF x, float d) {
+    const float q = __fdiv_rn(x.hi, d);
+    const float rem = __fadd_rn(__fmaf_rn(-q, d, x.hi), x.lo);
+    return two_sum(q, __fdiv_rn(rem, d));
+}
+
+// One coordinate of the pixel-centre ray, ((2 i + 1) / n - 1) / f, as a
+// double-float (2 i + 1 and n are exact floats below 2^24).
+__device__ __forceinline__ DF ray_coord(int i, int n, float f) {
+    DF t = df_div({__int2float_rn(2 * i + 1), 0.0f}, __int2float_rn(n));
+    t = df_add(t, {-1.0f, 0.0f});
+    return df_div(t, f);
+}
+
 // a b - c d for double-floats: the hi products error-free, their difference
 // as a double-float, the cross terms in FP32 (they are ulp-sized).
 __device__ __forceinline__ float df_cross1(DF a, DF b, DF c, DF d) {
@@ -294,8 +310,8 @@ __device__ __forceinline__ float df_cross1(DF a, DF b, DF c, DF d) {
 //   v_{j+1} x r = m + E_{j+1} x r,  r x v_{j-1} = -(m + E_{j-1} x r),
 // which are all well conditioned once m is: m alone carries the
 // cancellation, and is computed from v0 and r held as double-floats (v0 from
-// the FP32 model-view and position with error-free products, r from FP64)
-// with a compensated cross product.  The edges come from the model-space
+// the FP32 model-view and position with error-free products, r by
+// double-float division) with a compensated cross product.  The edges come from the model-space
 // differences rotated by M.  Everything else is plain FP32.
 __global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -326,10 +342,8 @@ __global__ void __launch_bounds__(256) k_interp_bwd(ShadeArgs a) {
             acc = df_add(acc, two_prod(mv[4 * r + 2], p0[2]));
             v0[r] = df_add(acc, {mv[4 * r + 3], 0.0f});
         }
-        // the pixel-centre ray in FP64, split into double-floats
-        const double rxd = ((2.0 * x + 1.0) / a.W - 1.0) / a.fx, ryd = ((2.0 * y + 1.0) / a.H - 1.0) / a.fy;
-        const DF rx = {(float)rxd, (float)(rxd - (double)(float)rxd)};
-        const DF ry = {(float)ryd, (float)(ryd - (double)(float)ryd)};
+        // the pixel-centre ray as double-floats
+        const DF rx = ray_coord(x, a.W, a.fx), ry = ray_coord(y, a.H, a.fy);
         const DF rz = {-1.0f, 0.0f};
         const float3 r = make_float3(rx.hi, ry.hi, -1.0f);
         // m = v0 x r

@@ -148,13 +148,27 @@ __device__ __forceinline__ float2 sub_x2(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
 
+// Minimum and maximum of three floats in one instruction each (the
+// three-input forms of min.f32 / max.f32); a NaN operand is ignored, as by
+// fminf / fmaxf.
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // fast_cull for two triangles of the same pair at once: the same arithmetic,
 // with the FMA rows, the products by 1/w, the margin and the widened bounds
 // evaluated on packed pairs (one triangle per half).  NEAR = false leaves the
 // near-plane test out (frames where no vertex can lie near that plane).
 template <bool NEAR = true>
 __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, const Tri9 &q, bool &cp, bool &cq) {
-    float2 xmn, xmx, ymn, ymx, wmn, wmx, rmx;
+    float2 X[3], Y[3], w[3], r[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float2 x = make_float2(p.v[3 * c], q.v[3 * c]);
@@ -163,21 +177,20 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
         const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw;
         const float2 xw = fma_x2(dup(rx.x), x, fma_x2(dup(rx.y), y, fma_x2(dup(rx.z), z, dup(rx.w))));
         const float2 yw = fma_x2(dup(ry.x), x, fma_x2(dup(ry.y), y, fma_x2(dup(ry.z), z, dup(ry.w))));
-        const float2 w = fma_x2(dup(rw.x), x, fma_x2(dup(rw.y), y, fma_x2(dup(rw.z), z, dup(rw.w))));
-        const float2 r = make_float2(rcp_approx(w.x), rcp_approx(w.y));
-        const float2 X = mul_x2(xw, r), Y = mul_x2(yw, r);
-        if (c == 0) {
-            xmn = xmx = X; ymn = ymx = Y; wmn = wmx = w; rmx = r;
-        } else {
-            xmn = make_float2(fminf(xmn.x, X.x), fminf(xmn.y, X.y));
-            xmx = make_float2(fmaxf(xmx.x, X.x), fmaxf(xmx.y, X.y));
-            ymn = make_float2(fminf(ymn.x, Y.x), fminf(ymn.y, Y.y));
-            ymx = make_float2(fmaxf(ymx.x, Y.x), fmaxf(ymx.y, Y.y));
-            wmn = make_float2(fminf(wmn.x, w.x), fminf(wmn.y, w.y));
-            if (NEAR) wmx = make_float2(fmaxf(wmx.x, w.x), fmaxf(wmx.y, w.y));
-            rmx = make_float2(fmaxf(rmx.x, r.x), fmaxf(rmx.y, r.y));
-        }
+        w[c] = fma_x2(dup(rw.x), x, fma_x2(dup(rw.y), y, fma_x2(dup(rw.z), z, dup(rw.w))));
+        r[c] = make_float2(rcp_approx(w[c].x), rcp_approx(w[c].y));
+        X[c] = mul_x2(xw, r[c]);
+        Y[c] = mul_x2(yw, r[c]);
     }
+    // bounds over the three vertices, one three-input min or max each
+    const float2 xmn = make_float2(min3f(X[0].x, X[1].x, X[2].x), min3f(X[0].y, X[1].y, X[2].y));
+    const float2 xmx = make_float2(max3f(X[0].x, X[1].x, X[2].x), max3f(X[0].y, X[1].y, X[2].y));
+    const float2 ymn = make_float2(min3f(Y[0].x, Y[1].x, Y[2].x), min3f(Y[0].y, Y[1].y, Y[2].y));
+    const float2 ymx = make_float2(max3f(Y[0].x, Y[1].x, Y[2].x), max3f(Y[0].y, Y[1].y, Y[2].y));
+    const float2 wmn = make_float2(min3f(w[0].x, w[1].x, w[2].x), min3f(w[0].y, w[1].y, w[2].y));
+    const float2 rmx = make_float2(max3f(r[0].x, r[1].x, r[2].x), max3f(r[0].y, r[1].y, r[2].y));
+    float2 wmx = wmn;
+    if (NEAR) wmx = make_float2(max3f(w[0].x, w[1].x, w[2].x), max3f(w[0].y, w[1].y, w[2].y));
     const float4 k = fp.k, lim = fp.lim;
     const float2 a = make_float2(fmaxf(fmaxf(fabsf(xmn.x), fabsf(xmx.x)), fmaxf(fabsf(ymn.x), fabsf(ymx.x))),
                                  fmaxf(fmaxf(fabsf(xmn.y), fabsf(xmx.y)), fmaxf(fabsf(ymn.y), fabsf(ymx.y))));
