@@ -97,6 +97,13 @@ __device__ __forceinline__ uint32_t mesh_index(const MeshDev &m, uint64_t k) {
     return m.imin + (__funnelshift_r(__ldg(w), __ldg(w + 1), (uint32_t)bit & 31u) & m.mask);
 }
 
+// A 16-bit value as a float, exactly: its bits OR-ed into the mantissa of
+// 2^23 give the float 2^23 + q, and subtracting 2^23 is exact (an OR and an
+// add instead of a conversion instruction).
+__device__ __forceinline__ float u16_to_float(uint32_t q) {
+    return __fsub_rn(__int_as_float(0x4B000000 | q), 8388608.0f);
+}
+
 // The three coordinates of vertex i as every stage renders them.
 __device__ __forceinline__ void mesh_vertex(const MeshDev &m, uint32_t i, float &x, float &y, float &z) {
     if (!m.qpos) {
@@ -104,9 +111,9 @@ __device__ __forceinline__ void mesh_vertex(const MeshDev &m, uint32_t i, float 
         x = __ldg(q); y = __ldg(q + 1); z = __ldg(q + 2);
     } else {
         const uint16_t *q = m.qpos + 3 * (uint64_t)i;
-        x = __fmaf_rn(__uint2float_rn(__ldg(q)), m.step[0], m.lo[0]);
-        y = __fmaf_rn(__uint2float_rn(__ldg(q + 1)), m.step[1], m.lo[1]);
-        z = __fmaf_rn(__uint2float_rn(__ldg(q + 2)), m.step[2], m.lo[2]);
+        x = __fmaf_rn(u16_to_float(__ldg(q)), m.step[0], m.lo[0]);
+        y = __fmaf_rn(u16_to_float(__ldg(q + 1)), m.step[1], m.lo[1]);
+        z = __fmaf_rn(u16_to_float(__ldg(q + 2)), m.step[2], m.lo[2]);
     }
 }
 

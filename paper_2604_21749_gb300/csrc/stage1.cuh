@@ -192,8 +192,8 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
     float2 wmx = wmn;
     if (NEAR) wmx = make_float2(max3f(w[0].x, w[1].x, w[2].x), max3f(w[0].y, w[1].y, w[2].y));
     const float4 k = fp.k, lim = fp.lim;
-    const float2 a = make_float2(fmaxf(fmaxf(fabsf(xmn.x), fabsf(xmx.x)), fmaxf(fabsf(ymn.x), fabsf(ymx.x))),
-                                 fmaxf(fmaxf(fabsf(xmn.y), fabsf(xmx.y)), fmaxf(fabsf(ymn.y), fabsf(ymx.y))));
+    const float2 a = make_float2(max3f(fabsf(xmn.x), fabsf(xmx.x), fmaxf(fabsf(ymn.x), fabsf(ymx.x))),
+                                 max3f(fabsf(xmn.y), fabsf(xmx.y), fmaxf(fabsf(ymn.y), fabsf(ymx.y))));
     const float2 m = fma_x2(rmx, fma_x2(dup(k.y), a, dup(k.x)), fma_x2(dup(k.z), a, dup(k.w)));
     const float2 xh = add_x2(xmx, m), xl = sub_x2(xmn, m), yh = add_x2(ymx, m), yl = sub_x2(ymn, m);
     const bool sp = (wmn.x > lim.x) & (a.x < lim.y), sq = (wmn.y > lim.x) & (a.y < lim.y);
@@ -467,6 +467,33 @@ __device__ __forceinline__ void stage1_producer(const FrameDev &f, s1::Smem<INST
     }
 }
 
+// The positions of the two triangles a lane holds, from a compressed mesh
+// (Section 4.6): the 16-bit values of both triangles' vertices, converted
+// exactly (as u16_to_float) and dequantized as fma(q, step, lo) with one
+// packed f32x2 operation per coordinate of the two -- each half rounds like
+// the scalar __fmaf_rn of mesh_vertex, so the positions are the same.
+__device__ __forceinline__ void decode_pair(const MeshDev &mesh, const uint32_t (&ix)[2][3], const bool (&valid)[2],
+                                            Tri9 (&p)[2]) {
+    uint32_t q[2][9];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint16_t *src = mesh.qpos + 3 * (uint64_t)ix[u][c];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) q[u][3 * c + a] = valid[u] ? (uint32_t)__ldg(src + a) : 0u;
+        }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int a = k % 3;
+        const float2 f = sub_x2(make_float2(__int_as_float(0x4B000000 | q[0][k]), __int_as_float(0x4B000000 | q[1][k])),
+                                dup(8388608.0f));
+        const float2 v = fma_x2(f, dup(mesh.step[a]), dup(mesh.lo[a]));
+        p[0].v[k] = valid[0] ? v.x : 0.0f;
+        p[1].v[k] = valid[1] ? v.y : 0.0f;
+    }
+}
+
 // Persistent stage-1 cull kernel, round r of the frame.  Consumers take one
 // triangle at a time: three index words from shared memory, nine position
 // floats from global memory, then for every pair of the item the
@@ -518,6 +545,9 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
         if (d.b >= rd.b1) break;
         const MeshDev mesh = S.mesh[slot];
         const uint32_t *idx = S.idx[slot];
+        // index bound as a 32-bit compare: every uint32 index is below V >= 2^32
+        const bool all_valid = mesh.V > 0xFFFFFFFFull;
+        const uint32_t v32 = (uint32_t)mesh.V;
         const uint32_t np = INST ? d.npairs : 1u;
         if (!FUSED) {
             // NT triangles per lane are loaded together (more loads in flight),
@@ -545,19 +575,19 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
                                                (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
                                 }
                             }
-                            if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= mesh.V) {
+                            if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= v32 && !all_valid) {
                                 if (f.check) atomicOr(f.err, kErrIndex);
                                 valid[u] = false;
                             }
                         }
                     }
                     Tri9 p[NT];
+                    if (comp) {
+                        decode_pair(mesh, ix, valid, p);
+                    } else
 #pragma unroll
                     for (int u = 0; u < NT; ++u) {
-                        if (valid[u] && comp) {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) mesh_vertex(mesh, ix[u][c], p[u].v[3 * c], p[u].v[3 * c + 1], p[u].v[3 * c + 2]);
-                        } else if (valid[u]) {
+                        if (valid[u]) {
 #pragma unroll
                             for (int c = 0; c < 3; ++c) {
                                 const float *q = mesh.pos + 3 * (uint64_t)ix[u][c];
@@ -606,19 +636,19 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
                                                (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
                                 }
                             }
-                            if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= mesh.V) {
+                            if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= v32 && !all_valid) {
                                 if (f.check) atomicOr(f.err, kErrIndex);
                                 valid[u] = false;
                             }
                         }
                     }
                     Tri9 p[NT];
+                    if (comp) {
+                        decode_pair(mesh, ix, valid, p);
+                    } else
 #pragma unroll
                     for (int u = 0; u < NT; ++u) {
-                        if (valid[u] && comp) {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) mesh_vertex(mesh, ix[u][c], p[u].v[3 * c], p[u].v[3 * c + 1], p[u].v[3 * c + 2]);
-                        } else if (valid[u]) {
+                        if (valid[u]) {
 #pragma unroll
                             for (int c = 0; c < 3; ++c) {
                                 const float *q = mesh.pos + 3 * (uint64_t)ix[u][c];
