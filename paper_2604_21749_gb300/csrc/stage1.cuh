@@ -162,35 +162,27 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
     return d;
 }
 
-// fast_cull for two triangles of the same pair at once: the same arithmetic,
-// with the FMA rows, the products by 1/w, the margin and the widened bounds
-// evaluated on packed pairs (one triangle per half).  NEAR = false leaves the
-// near-plane test out (frames where no vertex can lie near that plane).
-template <bool NEAR = true>
-__device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, const Tri9 &q, bool &cp, bool &cq) {
-    float2 X[3], Y[3], w[3], r[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float2 x = make_float2(p.v[3 * c], q.v[3 * c]);
-        const float2 y = make_float2(p.v[3 * c + 1], q.v[3 * c + 1]);
-        const float2 z = make_float2(p.v[3 * c + 2], q.v[3 * c + 2]);
-        const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw;
-        const float2 xw = fma_x2(dup(rx.x), x, fma_x2(dup(rx.y), y, fma_x2(dup(rx.z), z, dup(rx.w))));
-        const float2 yw = fma_x2(dup(ry.x), x, fma_x2(dup(ry.y), y, fma_x2(dup(ry.z), z, dup(ry.w))));
-        w[c] = fma_x2(dup(rw.x), x, fma_x2(dup(rw.y), y, fma_x2(dup(rw.z), z, dup(rw.w))));
-        r[c] = make_float2(rcp_approx(w[c].x), rcp_approx(w[c].y));
-        X[c] = mul_x2(xw, r[c]);
-        Y[c] = mul_x2(yw, r[c]);
-    }
-    // bounds over the three vertices, one three-input min or max each
-    const float2 xmn = make_float2(min3f(X[0].x, X[1].x, X[2].x), min3f(X[0].y, X[1].y, X[2].y));
-    const float2 xmx = make_float2(max3f(X[0].x, X[1].x, X[2].x), max3f(X[0].y, X[1].y, X[2].y));
-    const float2 ymn = make_float2(min3f(Y[0].x, Y[1].x, Y[2].x), min3f(Y[0].y, Y[1].y, Y[2].y));
-    const float2 ymx = make_float2(max3f(Y[0].x, Y[1].x, Y[2].x), max3f(Y[0].y, Y[1].y, Y[2].y));
-    const float2 wmn = make_float2(min3f(w[0].x, w[1].x, w[2].x), min3f(w[0].y, w[1].y, w[2].y));
-    const float2 rmx = make_float2(max3f(r[0].x, r[1].x, r[2].x), max3f(r[0].y, r[1].y, r[2].y));
-    float2 wmx = wmn;
-    if (NEAR) wmx = make_float2(max3f(w[0].x, w[1].x, w[2].x), max3f(w[0].y, w[1].y, w[2].y));
+// The rows of the conservative cull for two vertices at once (one per half
+// of each packed pair): X'w, Y'w and w by FMA, 1/w by rcp.approx, then
+// X' = (X'w)(1/w) and Y' = (Y'w)(1/w).
+__device__ __forceinline__ void xform2(const FastPair &fp, float2 x, float2 y, float2 z, float2 &X, float2 &Y,
+                                       float2 &w, float2 &r) {
+    const float4 rx = fp.rx, ry = fp.ry, rw = fp.rw;
+    const float2 xw = fma_x2(dup(rx.x), x, fma_x2(dup(rx.y), y, fma_x2(dup(rx.z), z, dup(rx.w))));
+    const float2 yw = fma_x2(dup(ry.x), x, fma_x2(dup(ry.y), y, fma_x2(dup(ry.z), z, dup(ry.w))));
+    w = fma_x2(dup(rw.x), x, fma_x2(dup(rw.y), y, fma_x2(dup(rw.z), z, dup(rw.w))));
+    r = make_float2(rcp_approx(w.x), rcp_approx(w.y));
+    X = mul_x2(xw, r);
+    Y = mul_x2(yw, r);
+}
+
+// The decision of the conservative cull for two triangles (one per half)
+// from their vertices' bounds: the margin m, the widened bounds, the
+// pixel-centre test on each axis, the region where the bound holds and, with
+// NEAR, every vertex beyond the near plane.
+template <bool NEAR>
+__device__ __forceinline__ void cull_tail2(const FastPair &fp, float2 xmn, float2 xmx, float2 ymn, float2 ymx,
+                                           float2 wmn, float2 wmx, float2 rmx, bool &cp, bool &cq) {
     const float4 k = fp.k, lim = fp.lim;
     const float2 a = make_float2(max3f(fabsf(xmn.x), fabsf(xmx.x), fmaxf(fabsf(ymn.x), fabsf(ymx.x))),
                                  max3f(fabsf(xmn.y), fabsf(xmx.y), fmaxf(fabsf(ymn.y), fabsf(ymx.y))));
@@ -205,6 +197,39 @@ __device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, co
         cp |= wmx.x < fp.sl.w;
         cq |= wmx.y < fp.sl.w;
     }
+}
+
+// fast_cull for two triangles of the same pair at once: the same arithmetic,
+// with the FMA rows, the products by 1/w, the margin and the widened bounds
+// evaluated on packed pairs (one triangle per half).  NEAR = false leaves the
+// near-plane test out (frames where no vertex can lie near that plane).
+template <bool NEAR = true>
+__device__ __forceinline__ void fast_cull2(const FastPair &fp, const Tri9 &p, const Tri9 &q, bool &cp, bool &cq) {
+    float2 X[3], Y[3], w[3], r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        xform2(fp, make_float2(p.v[3 * c], q.v[3 * c]), make_float2(p.v[3 * c + 1], q.v[3 * c + 1]),
+               make_float2(p.v[3 * c + 2], q.v[3 * c + 2]), X[c], Y[c], w[c], r[c]);
+    // bounds over the three vertices, one three-input min or max each
+    const float2 xmn = make_float2(min3f(X[0].x, X[1].x, X[2].x), min3f(X[0].y, X[1].y, X[2].y));
+    const float2 xmx = make_float2(max3f(X[0].x, X[1].x, X[2].x), max3f(X[0].y, X[1].y, X[2].y));
+    const float2 ymn = make_float2(min3f(Y[0].x, Y[1].x, Y[2].x), min3f(Y[0].y, Y[1].y, Y[2].y));
+    const float2 ymx = make_float2(max3f(Y[0].x, Y[1].x, Y[2].x), max3f(Y[0].y, Y[1].y, Y[2].y));
+    const float2 wmn = make_float2(min3f(w[0].x, w[1].x, w[2].x), min3f(w[0].y, w[1].y, w[2].y));
+    const float2 rmx = make_float2(max3f(r[0].x, r[1].x, r[2].x), max3f(r[0].y, r[1].y, r[2].y));
+    float2 wmx = wmn;
+    if (NEAR) wmx = make_float2(max3f(w[0].x, w[1].x, w[2].x), max3f(w[0].y, w[1].y, w[2].y));
+    cull_tail2<NEAR>(fp, xmn, xmx, ymn, ymx, wmn, wmx, rmx, cp, cq);
+}
+
+// The bounds of two triangles of a strip (one per half) whose vertices are
+// the consecutive vertices (a, b, c) and (b, c, d) of the strip, given as the
+// packed pairs ab = (a, b) and cd = (c, d) of one quantity.
+__device__ __forceinline__ float2 strip_min(float2 ab, float2 cd) {
+    return make_float2(min3f(ab.x, ab.y, cd.x), min3f(ab.y, cd.x, cd.y));
+}
+__device__ __forceinline__ float2 strip_max(float2 ab, float2 cd) {
+    return make_float2(max3f(ab.x, ab.y, cd.x), max3f(ab.y, cd.x, cd.y));
 }
 
 // The same test for a whole group of triangles and one pair, from the
@@ -494,6 +519,103 @@ __device__ __forceinline__ void decode_pair(const MeshDev &mesh, const uint32_t 
     }
 }
 
+// Single-pair items of plain meshes, four consecutive triangles a lane: a
+// warp takes the 128-triangle groups g = warp, warp + 8, ... of the item and
+// lane l the triangles 128 g + 4 l .. 128 g + 4 l + 3, whose twelve index
+// words are three 16-byte loads from shared memory.  Where the four are in
+// strip order -- the list a triangle strip s0 s1 s2 s3 s4 s5 unrolls to,
+// (s0 s1 s2) (s2 s1 s3) (s2 s3 s4) (s4 s3 s5), which is how a row-major grid
+// mesh lists a row of cells -- triangle k has the vertices s_k, s_k+1 and
+// s_k+2; when every lane's four are, the warp loads and transforms the six
+// vertices once for the four triangles.  The cull's bounds are symmetric in
+// a triangle's vertices, so each triangle gets the decision fast_cull2 would
+// give it.  Other orders run fast_cull2 on the two pairs of triangles.  The
+// 128 decisions are the bitmap words 4 g .. 4 g + 3 of the item (word h:
+// triangles 128 g + 32 h + b at bit b), gathered by OR-reductions and stored
+// at once.
+template <bool NEAR>
+__device__ __forceinline__ void cull_quads(const FrameDev &f, const uint32_t *idx, const FastPair &fp,
+                                           const MeshDev &mesh, const s1::Desc &d, uint32_t tpt, int warp, int lane) {
+    using namespace s1;
+    const bool all_valid = mesh.V > 0xFFFFFFFFull;   // every uint32 index is below V
+    const uint32_t v32 = (uint32_t)mesh.V;
+    const float *pos = mesh.pos;
+    for (uint32_t g = warp; g < 2 * tpt; g += kConsumerWarps) {   // the warp stays converged
+        const uint32_t lt = 128 * g + 4 * lane;
+        const uint4 *src = reinterpret_cast<const uint4 *>(idx + 3 * lt);
+        const uint4 ia = src[0], ib = src[1], ic = src[2];
+        const uint32_t ix[12] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w, ic.x, ic.y, ic.z, ic.w};
+        bool valid[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            valid[u] = lt + u < d.n;
+            if (valid[u] && !all_valid && max(ix[3 * u], max(ix[3 * u + 1], ix[3 * u + 2])) >= v32) {
+                if (f.check) atomicOr(f.err, kErrIndex);
+                valid[u] = false;
+            }
+        }
+        const bool strip = valid[0] & valid[1] & valid[2] & valid[3] & (ix[3] == ix[2]) & (ix[4] == ix[1]) &
+                           (ix[6] == ix[2]) & (ix[7] == ix[5]) & (ix[9] == ix[8]) & (ix[10] == ix[5]);
+        bool cull[4];
+        if (__all_sync(0xffffffffu, strip)) {
+            const uint32_t sv[6] = {ix[0], ix[1], ix[2], ix[5], ix[8], ix[11]};
+            float v[18];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const float *q = pos + 3 * (uint64_t)sv[c];
+                v[3 * c] = __ldg(q); v[3 * c + 1] = __ldg(q + 1); v[3 * c + 2] = __ldg(q + 2);
+            }
+            // vertex pairs (s0, s1), (s2, s3), (s4, s5)
+            float2 X[3], Y[3], w[3], r[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                xform2(fp, make_float2(v[6 * c], v[6 * c + 3]), make_float2(v[6 * c + 1], v[6 * c + 4]),
+                       make_float2(v[6 * c + 2], v[6 * c + 5]), X[c], Y[c], w[c], r[c]);
+            // triangles (t0, t1) from the pairs (s0, s1), (s2, s3); (t2, t3) from (s2, s3), (s4, s5)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                cull_tail2<NEAR>(fp, strip_min(X[h], X[h + 1]), strip_max(X[h], X[h + 1]), strip_min(Y[h], Y[h + 1]),
+                                 strip_max(Y[h], Y[h + 1]), strip_min(w[h], w[h + 1]),
+                                 NEAR ? strip_max(w[h], w[h + 1]) : make_float2(0.0f, 0.0f),
+                                 strip_max(r[h], r[h + 1]), cull[2 * h], cull[2 * h + 1]);
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                Tri9 p[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (valid[2 * h + u]) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float *q = pos + 3 * (uint64_t)idx[3 * (lt + 2 * h + u) + c];   // (read again)
+                            p[u].v[3 * c] = __ldg(q); p[u].v[3 * c + 1] = __ldg(q + 1); p[u].v[3 * c + 2] = __ldg(q + 2);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
+                    }
+                }
+                fast_cull2<NEAR>(fp, p[0], p[1], cull[2 * h], cull[2 * h + 1]);
+            }
+        }
+        uint32_t nib = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool live = valid[u] && !cull[u];
+            if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
+            nib |= (uint32_t)live << u;
+        }
+        const uint32_t sh = nib << (4 * (lane & 7)), h = (uint32_t)lane >> 3;
+        uint4 wd;
+        wd.x = __reduce_or_sync(0xffffffffu, h == 0 ? sh : 0u);
+        wd.y = __reduce_or_sync(0xffffffffu, h == 1 ? sh : 0u);
+        wd.z = __reduce_or_sync(0xffffffffu, h == 2 ? sh : 0u);
+        wd.w = __reduce_or_sync(0xffffffffu, h == 3 ? sh : 0u);
+        // 16-byte aligned: the item's words start at a multiple of 8 tpt
+        if (lane == 0) *reinterpret_cast<uint4 *>(f.bits + d.wbase + 4 * g) = wd;
+    }
+}
+
 // Persistent stage-1 cull kernel, round r of the frame.  Consumers take one
 // triangle at a time: three index words from shared memory, nine position
 // floats from global memory, then for every pair of the item the
@@ -555,7 +677,9 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
             // read from shared memory, which leaves the registers to the loads
             constexpr int NT = kNT;
             constexpr bool comp = COMP;                   // rounds hold one kind of mesh
-            if constexpr (!INST) {
+            if constexpr (!INST && !COMP) {
+                cull_quads<NEAR>(f, idx, S.fp[slot][0], mesh, d, tpt, warp, lane);
+            } else if constexpr (!INST) {
                 for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
                     bool valid[NT];
                     uint32_t ix[NT][3];
