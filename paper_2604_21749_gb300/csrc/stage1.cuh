@@ -532,8 +532,10 @@ __device__ __forceinline__ void decode_pair(const MeshDev &mesh, const uint32_t 
 // give it.  Other orders run fast_cull2 on the two pairs of triangles.  The
 // 128 decisions are the bitmap words 4 g .. 4 g + 3 of the item (word h:
 // triangles 128 g + 32 h + b at bit b), gathered by OR-reductions and stored
-// at once.
-template <bool NEAR>
+// at once.  Compressed meshes (COMP, Section 4.6) decode the twelve index
+// fields of a lane from the packed bits, and in strip order only the six
+// vertices' 16-bit positions.
+template <bool NEAR, bool COMP>
 __device__ __forceinline__ void cull_quads(const FrameDev &f, const uint32_t *idx, const FastPair &fp,
                                            const MeshDev &mesh, const s1::Desc &d, uint32_t tpt, int warp, int lane) {
     using namespace s1;
@@ -542,35 +544,61 @@ __device__ __forceinline__ void cull_quads(const FrameDev &f, const uint32_t *id
     const float *pos = mesh.pos;
     for (uint32_t g = warp; g < 2 * tpt; g += kConsumerWarps) {   // the warp stays converged
         const uint32_t lt = 128 * g + 4 * lane;
-        const uint4 *src = reinterpret_cast<const uint4 *>(idx + 3 * lt);
-        const uint4 ia = src[0], ib = src[1], ic = src[2];
-        const uint32_t ix[12] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w, ic.x, ic.y, ic.z, ic.w};
-        bool valid[4];
+        uint32_t ix[12];
+        if constexpr (!COMP) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(idx + 3 * lt);
+            const uint4 ia = src[0], ib = src[1], ic = src[2];
+            ix[0] = ia.x; ix[1] = ia.y; ix[2] = ia.z; ix[3] = ia.w; ix[4] = ib.x; ix[5] = ib.y;
+            ix[6] = ib.z; ix[7] = ib.w; ix[8] = ic.x; ix[9] = ic.y; ix[10] = ic.z; ix[11] = ic.w;
+        } else {
+            // index 3 lt + k of the item sits at bit (3 lt + k) bits of the slot
+            uint32_t bit = 3 * lt * mesh.bits;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            valid[u] = lt + u < d.n;
-            if (valid[u] && !all_valid && max(ix[3 * u], max(ix[3 * u + 1], ix[3 * u + 2])) >= v32) {
-                if (f.check) atomicOr(f.err, kErrIndex);
-                valid[u] = false;
-            }
+            for (int k = 0; k < 12; ++k, bit += mesh.bits)
+                ix[k] = mesh.imin + (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
         }
-        const bool strip = valid[0] & valid[1] & valid[2] & valid[3] & (ix[3] == ix[2]) & (ix[4] == ix[1]) &
+        const uint32_t smax = max(max(ix[0], max(ix[1], ix[2])), max(ix[5], max(ix[8], ix[11])));
+        const bool strip = (lt + 3 < d.n) & (all_valid | (smax < v32)) & (ix[3] == ix[2]) & (ix[4] == ix[1]) &
                            (ix[6] == ix[2]) & (ix[7] == ix[5]) & (ix[9] == ix[8]) & (ix[10] == ix[5]);
         bool cull[4];
+        bool valid[4] = {true, true, true, true};
         if (__all_sync(0xffffffffu, strip)) {
             const uint32_t sv[6] = {ix[0], ix[1], ix[2], ix[5], ix[8], ix[11]};
-            float v[18];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                const float *q = pos + 3 * (uint64_t)sv[c];
-                v[3 * c] = __ldg(q); v[3 * c + 1] = __ldg(q + 1); v[3 * c + 2] = __ldg(q + 2);
-            }
             // vertex pairs (s0, s1), (s2, s3), (s4, s5)
             float2 X[3], Y[3], w[3], r[3];
+            if constexpr (!COMP) {
+                float v[18];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                xform2(fp, make_float2(v[6 * c], v[6 * c + 3]), make_float2(v[6 * c + 1], v[6 * c + 4]),
-                       make_float2(v[6 * c + 2], v[6 * c + 5]), X[c], Y[c], w[c], r[c]);
+                for (int c = 0; c < 6; ++c) {
+                    const float *q = pos + 3 * (uint64_t)sv[c];
+                    v[3 * c] = __ldg(q); v[3 * c + 1] = __ldg(q + 1); v[3 * c + 2] = __ldg(q + 2);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    xform2(fp, make_float2(v[6 * c], v[6 * c + 3]), make_float2(v[6 * c + 1], v[6 * c + 4]),
+                           make_float2(v[6 * c + 2], v[6 * c + 5]), X[c], Y[c], w[c], r[c]);
+            } else {
+                // the 16-bit values, converted exactly (as u16_to_float) and
+                // dequantized as fma(q, step, lo), two vertices a packed pair
+                uint32_t q[18];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const uint16_t *src = mesh.qpos + 3 * (uint64_t)sv[c];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) q[3 * c + a] = (uint32_t)__ldg(src + a);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float2 p[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        p[a] = fma_x2(sub_x2(make_float2(__int_as_float(0x4B000000 | q[6 * c + a]),
+                                                         __int_as_float(0x4B000000 | q[6 * c + 3 + a])),
+                                             dup(8388608.0f)),
+                                      dup(mesh.step[a]), dup(mesh.lo[a]));
+                    xform2(fp, p[0], p[1], p[2], X[c], Y[c], w[c], r[c]);
+                }
+            }
             // triangles (t0, t1) from the pairs (s0, s1), (s2, s3); (t2, t3) from (s2, s3), (s4, s5)
 #pragma unroll
             for (int h = 0; h < 2; ++h)
@@ -580,8 +608,22 @@ __device__ __forceinline__ void cull_quads(const FrameDev &f, const uint32_t *id
                                  strip_max(r[h], r[h + 1]), cull[2 * h], cull[2 * h + 1]);
         } else {
 #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                valid[u] = lt + u < d.n;
+                if (valid[u] && !all_valid && max(ix[3 * u], max(ix[3 * u + 1], ix[3 * u + 2])) >= v32) {
+                    if (f.check) atomicOr(f.err, kErrIndex);
+                    valid[u] = false;
+                }
+            }
+#pragma unroll
             for (int h = 0; h < 2; ++h) {
                 Tri9 p[2];
+                if constexpr (COMP) {
+                    const uint32_t pix[2][3] = {{ix[6 * h], ix[6 * h + 1], ix[6 * h + 2]},
+                                                {ix[6 * h + 3], ix[6 * h + 4], ix[6 * h + 5]}};
+                    const bool pv[2] = {valid[2 * h], valid[2 * h + 1]};
+                    decode_pair(mesh, pix, pv, p);
+                } else
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     if (valid[2 * h + u]) {
@@ -616,13 +658,14 @@ __device__ __forceinline__ void cull_quads(const FrameDev &f, const uint32_t *id
     }
 }
 
-// Persistent stage-1 cull kernel, round r of the frame.  Consumers take one
-// triangle at a time: three index words from shared memory, nine position
-// floats from global memory, then for every pair of the item the
-// conservative tiny-triangle cull.  The warp's ballot of the triangles it
-// keeps is stored as one word of the survivor bitmap (32 consecutive
-// triangles of one pair), which k_stage1_exact works through afterwards;
-// the cull stays free of the exact path's registers.  The FUSED form (no
+// Persistent stage-1 cull kernel, round r of the frame.  Consumers read
+// index words from shared memory and position floats from global memory,
+// then run the conservative tiny-triangle cull for every pair of the item
+// (single-pair items: four consecutive triangles a lane, cull_quads;
+// instanced items: two a lane, looped over the pairs).  The warp's
+// decisions are stored as words of the survivor bitmap (32 consecutive
+// triangles of one pair a word), which k_stage1_exact works through
+// afterwards; the cull stays free of the exact path's registers.  The FUSED form (no
 // bitmap) queues the survivors per warp and runs the exact path itself,
 // 32 at a time.  INST blocks loop over many pairs (Section 4.5, extended to
 // several views): a triangle's data is loaded once for all of them.
@@ -677,70 +720,13 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
             // read from shared memory, which leaves the registers to the loads
             constexpr int NT = kNT;
             constexpr bool comp = COMP;                   // rounds hold one kind of mesh
-            if constexpr (!INST && !COMP) {
-                cull_quads<NEAR>(f, idx, S.fp[slot][0], mesh, d, tpt, warp, lane);
-            } else if constexpr (!INST) {
-                for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
-                    bool valid[NT];
-                    uint32_t ix[NT][3];
-#pragma unroll
-                    for (int u = 0; u < NT; ++u) {
-                        const uint32_t lt = (k + u) * kConsumers + tid;
-                        valid[u] = k + u < tpt && lt < d.n;
-                        ix[u][0] = ix[u][1] = ix[u][2] = 0;
-                        if (valid[u]) {
-                            if (!comp) {
-                                ix[u][0] = idx[3 * lt]; ix[u][1] = idx[3 * lt + 1]; ix[u][2] = idx[3 * lt + 2];
-                            } else {
-#pragma unroll
-                                for (int c = 0; c < 3; ++c) {
-                                    const uint32_t bit = (3 * lt + c) * mesh.bits;
-                                    ix[u][c] = mesh.imin +
-                                               (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
-                                }
-                            }
-                            if (max(ix[u][0], max(ix[u][1], ix[u][2])) >= v32 && !all_valid) {
-                                if (f.check) atomicOr(f.err, kErrIndex);
-                                valid[u] = false;
-                            }
-                        }
-                    }
-                    Tri9 p[NT];
-                    if (comp) {
-                        decode_pair(mesh, ix, valid, p);
-                    } else
-#pragma unroll
-                    for (int u = 0; u < NT; ++u) {
-                        if (valid[u]) {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const float *q = mesh.pos + 3 * (uint64_t)ix[u][c];
-                                p[u].v[3 * c] = __ldg(q); p[u].v[3 * c + 1] = __ldg(q + 1); p[u].v[3 * c + 2] = __ldg(q + 2);
-                            }
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
-                        }
-                    }
-                    for (uint32_t pi = 0; pi < np; ++pi) {
-                        bool cull[NT];
-                        static_assert(NT == 2, "the cull evaluates triangles in packed pairs");
-                        fast_cull2<NEAR>(S.fp[slot][pi], p[0], p[1], cull[0], cull[1]);
-#pragma unroll
-                        for (int u = 0; u < NT; ++u) {
-                            const bool live = valid[u] && !cull[u];
-                            if (f.stats && valid[u] && !live) stat_add(f, kStatIn, 1), stat_add(f, kStatTiny, 1);
-                            const unsigned m = __ballot_sync(0xffffffffu, live);
-                            if (k + u < tpt && lane == 0) f.bits[d.wbase + pi * G + (k + u) * kConsumerWarps + warp] = m;
-                        }
-                    }
-                }
+            if constexpr (!INST) {
+                cull_quads<NEAR, COMP>(f, idx, S.fp[slot][0], mesh, d, tpt, warp, lane);
             } else {
-                // A lane takes one triangle of each of nv 32-triangle runs a
-                // step; the warp's ballot over run q is bitmap word q of the
-                // pair.  Single-pair items take runs (k + u) * 8 + warp; the
-                // instanced ones, whose group test wants the step's triangles
-                // together, the adjacent runs k * 8 + nv * warp + u.
+                // Instanced items: a lane takes one triangle of each of nv
+                // 32-triangle runs a step, the adjacent runs k * 8 + nv * warp
+                // + u (the group test wants the step's triangles together);
+                // the warp's ballot over run q is bitmap word q of the pair.
                 for (uint32_t k = 0; k < tpt; k += NT) {   // uniform trip count: the warp stays converged
                     bool valid[NT];
                     uint32_t ix[NT][3];
