@@ -360,8 +360,8 @@ constexpr int kSlots = 3;
 constexpr int kQueue = 64;                           // per-warp survivors (fused kernel)
 constexpr int kMaxPairs = 64;                        // pairs of one segment (pairs_per_segment <= 64)
 constexpr int kNT = 2;                               // triangles a lane loads together
-constexpr int kCullBlocks = 4;                       // single-pair cull blocks per SM: 56 registers a thread
-                                                     // (instanced and fused: 3, 72 registers)
+constexpr int kCullBlocks = 3;                       // cull blocks per SM: 72 registers a thread (at 4 blocks
+                                                     // and 56 registers the four-triangle cull spills)
 
 struct Desc {
     unsigned long long b;  // work item, >= the round's end: none (consumers stop)
