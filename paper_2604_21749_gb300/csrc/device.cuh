@@ -51,6 +51,17 @@ struct PairDev {             // one (instance, view) pair that survived host cul
     uint32_t mesh;
 };
 
+// Constants of the division of 32-bit numbers by a fixed d >= 2 with a
+// multiply-high (Granlund and Montgomery, unsigned division by invariant
+// integers): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, s = l - 1;
+// then n / d = (t + ((n - t) >> 1)) >> s with t = mulhi(n, m).
+__host__ __device__ inline void fastdiv_consts(uint32_t d, uint32_t &m, uint32_t &s) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1ull);
+    s = l - 1u;
+}
+
 struct SegDev {              // a stage-1 work item: one mesh x a run of its pairs
     uint32_t mesh;
     uint32_t pair0;
@@ -173,6 +184,7 @@ struct FrameDev {
     uint32_t s2_max;         // stage-2 bbox pixel limit
     uint32_t tile_log2;
     uint32_t tpt;            // stage-1 triangles per thread per grab
+    uint32_t g_m, g_s;       // multiply-high division by G = 8 tpt words (fastdiv_consts)
     uint32_t check;          // bounds-check indices
     uint32_t stats;          // count statistics
     uint32_t group_min;      // instanced items with >= this many pairs (> 0) run the group test

@@ -204,7 +204,14 @@ constexpr int kOutside = (int)0x80000000;
 
 __device__ __forceinline__ Rec make_rec(CV c, const ViewDev &vw) {
     Rec r;
-    const unsigned oc = outcode(c, vw.nearv);
+    // Inside every plane, decided without the five plane values: w >= near,
+    // |x| <= 128 w and |y| <= 128 w give the same answers as the signs of
+    // w - near, x + 128 w, ... (a sum of two finite floats rounds to zero only
+    // when it is zero; no flush to zero here), NaN fails both forms, and an
+    // infinite 128 w takes the full outcode (inf - inf is NaN there).
+    const float gw = __fmul_rn(kGuard, c.w);
+    const bool inside = (c.w >= vw.nearv) & (gw < INFINITY) & (fabsf(c.x) <= gw) & (fabsf(c.y) <= gw);
+    const unsigned oc = inside ? 0u : outcode(c, vw.nearv);
     if (oc) {
         r.X = kOutside;
         r.Y = (int)oc;

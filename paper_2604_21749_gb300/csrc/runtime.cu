@@ -612,6 +612,7 @@ FrameDev make_frame_dev(const curast_ctx *c) {
     f.s2_max = c->cfg.stage2_max_pixels;
     f.tile_log2 = c->cfg.tile_log2;
     f.tpt = c->cfg.stage1_tri_per_thread;
+    fastdiv_consts(8u * f.tpt, f.g_m, f.g_s);
     f.group_min = c->cfg.stage1_group_min_pairs;
     f.s3_ray = c->cfg.stage3_raycast;
     f.check = c->cfg.check_indices;

@@ -901,6 +901,11 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
 // issues the index and position loads of its kExactK survivors before any
 // arithmetic), parked in shared memory, and run through the exact path one
 // survivor a lane at a time.
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, uint32_t m, uint32_t sh) {   // (fastdiv_consts)
+    const uint32_t t = __umulhi(n, m);
+    return (t + ((n - t) >> 1)) >> sh;
+}
+
 namespace s1 {
 constexpr int kExactWarps = 4;
 constexpr int kExactBlocks = 5;                      // 96 registers a thread
@@ -944,9 +949,18 @@ __global__ void __launch_bounds__(32 * s1::kExactWarps, s1::kExactBlocks)
                         const SegDev &sg = f.segs[sl];
                         const uint64_t local = gw - sg.word0;
                         const uint32_t per = sg.npairs * G;         // words per item (<= 64 * 32)
-                        const uint64_t jb = local < (1ull << 32) ? (uint64_t)((uint32_t)local / per) : local / per;
-                        const uint32_t rem = (uint32_t)(local - jb * per);
-                        const uint32_t pi = rem / G, g = rem - pi * G;
+                        uint64_t jb;
+                        uint32_t pi, g;
+                        if (sg.npairs == 1 && local < (1ull << 32)) {   // one pair: item and group
+                            jb = fastdiv((uint32_t)local, f.g_m, f.g_s);
+                            g = (uint32_t)local - (uint32_t)jb * G;
+                            pi = 0;
+                        } else {
+                            jb = local < (1ull << 32) ? (uint64_t)((uint32_t)local / per) : local / per;
+                            const uint32_t rem = (uint32_t)(local - jb * per);
+                            pi = rem / G;
+                            g = rem - pi * G;
+                        }
                         t0 = jb * per_item + 32ull * g;
                         pair = sg.pair0 + pi;
                     }

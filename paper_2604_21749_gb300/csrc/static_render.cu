@@ -213,6 +213,7 @@ extern "C" curast_status curast_render_static(const float *pos, uint64_t V, cons
     f.s2_max = 4096;
     f.tile_log2 = 6;
     f.tpt = 4;
+    fastdiv_consts(8u * f.tpt, f.g_m, f.g_s);
     f.group_min = 0;
     f.s3_ray = 0;
     f.check = 1;
