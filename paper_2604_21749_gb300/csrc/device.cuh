@@ -392,15 +392,41 @@ __device__ __forceinline__ bool pixel_key(const SubTri &s, int x, int y, uint64_
 
 // Pixels i = start, start + stride, ... of the sub-triangle's pixel range
 // (x = x0 + i mod w, y = y0 + i / w: the 1D loop of Section 4.2), optionally
-// restricted to a sub-rectangle.
+// restricted to a sub-rectangle.  The int64 edge functions of shade_pixel are
+// evaluated at the thread's first pixel and then stepped exactly: a step of
+// `stride` pixels is q rows and r columns (stride = q w + r), one column
+// changes E_k by -256 dy_k and one row by +256 dx_k, and a column past x1
+// wraps to the next row.
 __device__ __forceinline__ void raster_range(const SubTri &s, int x0, int x1, int y0, int y1, int start, int stride,
                                              uint64_t *vis, int W) {
     const int w = x1 - x0 + 1;
     const int64_t n = (int64_t)w * (int64_t)(y1 - y0 + 1);
+    if ((int64_t)start >= n) return;
+    int y = y0 + start / w, x = x0 + start % w;
+    const int q = stride / w, r = stride % w;
+    const int64_t px = 256 * (int64_t)x + 128, py = 256 * (int64_t)y + 128;
+    const int64_t dx0 = (int64_t)s.X[2] - s.X[1], dy0 = (int64_t)s.Y[2] - s.Y[1];
+    const int64_t dx1 = (int64_t)s.X[0] - s.X[2], dy1 = (int64_t)s.Y[0] - s.Y[2];
+    const int64_t dx2 = (int64_t)s.X[1] - s.X[0], dy2 = (int64_t)s.Y[1] - s.Y[0];
+    int64_t E0 = dx0 * (py - s.Y[1]) - dy0 * (px - s.X[1]);
+    int64_t E1 = dx1 * (py - s.Y[2]) - dy1 * (px - s.X[2]);
+    int64_t E2 = dx2 * (py - s.Y[0]) - dy2 * (px - s.X[0]);
+    const int64_t S0 = 256 * ((int64_t)q * dx0 - (int64_t)r * dy0), S1 = 256 * ((int64_t)q * dx1 - (int64_t)r * dy1),
+                  S2 = 256 * ((int64_t)q * dx2 - (int64_t)r * dy2);
+    const int64_t R0 = 256 * (dx0 + (int64_t)w * dy0), R1 = 256 * (dx1 + (int64_t)w * dy1),
+                  R2 = 256 * (dx2 + (int64_t)w * dy2);
+    const int64_t b0 = s.bias & 1u, b1 = (s.bias >> 1) & 1u, b2 = (s.bias >> 2) & 1u;
     for (int64_t i = start; i < n; i += stride) {
-        const int y = y0 + (int)(i / w);
-        const int x = x0 + (int)(i - (int64_t)(y - y0) * w);
-        shade_pixel(s, x, y, vis, W);
+        if (((E0 - b0) | (E1 - b1) | (E2 - b2)) >= 0)
+            depth_test_write(vis, (size_t)y * (size_t)W + (size_t)x, frag_key(E0, E1, E2, s.A, s.iz, s.id));
+        x += r;
+        y += q;
+        E0 += S0; E1 += S1; E2 += S2;
+        if (x > x1) {
+            x -= w;
+            ++y;
+            E0 += R0; E1 += R1; E2 += R2;
+        }
     }
 }
 
