@@ -202,6 +202,13 @@ typedef struct {
     uint64_t geometry_bytes;      /* device bytes of the index and position data a frame reads */
     const void *packed_indices;   /* device: ceil(3 T bits / 32) words, then zero padding     */
     const void *quantized_positions; /* device: V x 3 uint16                                  */
+    const void *grid_flags;       /* device: ceil(ceil(T / 128) / 32) uint32 words; bit G (word
+                                     G / 32, bit G % 32) set when the 128 triangles 128 G ..
+                                     128 G + 127 all exist and each run of four, 128 G + 4 l ..
+                                     + 3, lists (s0 s1 s2) (s2 s1 s3) (s2 s3 s4) (s4 s3 s5) with
+                                     s2 = s0 + 1, s4 = s0 + 2, s3 = s1 + 1, s5 = s1 + 2, all
+                                     below V (a row of a row-major grid): the compressed cull
+                                     then decodes s0 and s1 alone (compressed meshes)         */
 } curast_mesh_info;
 
 curast_status curast_get_mesh_info(const curast_ctx *ctx, uint32_t mesh_id, curast_mesh_info *out);

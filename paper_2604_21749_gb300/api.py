@@ -71,7 +71,8 @@ class Stats(C.Structure):
 class MeshInfo(C.Structure):
     _fields_ = [("V", C.c_uint64), ("T", C.c_uint64), ("compressed", C.c_uint32), ("index_bits", C.c_uint32),
                 ("index_min", C.c_uint32), ("pad", C.c_uint32), ("pos_lo", C.c_float * 3), ("pos_step", C.c_float * 3),
-                ("geometry_bytes", C.c_uint64), ("packed_indices", C.c_void_p), ("quantized_positions", C.c_void_p)]
+                ("geometry_bytes", C.c_uint64), ("packed_indices", C.c_void_p), ("quantized_positions", C.c_void_p),
+                ("grid_flags", C.c_void_p)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}

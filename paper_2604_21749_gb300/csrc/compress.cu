@@ -62,6 +62,44 @@ __global__ void __launch_bounds__(256) k_quantize_positions(const float *pos, ui
     }
 }
 
+// Grid flags of a compressed mesh, bit k of word w for the 128-triangle
+// group G = 32 w + k: set when the group lies wholly inside the mesh and each
+// of its 32 runs of four triangles, 4 l .. 4 l + 3, lists the strip of a
+// row-major grid, (s0 s1 s2) (s2 s1 s3) (s2 s3 s4) (s4 s3 s5) with s2 = s0 + 1,
+// s4 = s0 + 2, s3 = s1 + 1, s5 = s1 + 2, every index below V.  The cull then
+// decodes s0 and s1 alone and knows the other ten index fields.  One warp a
+// word.
+__global__ void __launch_bounds__(256) k_grid_flags(const uint32_t *idx, uint64_t T, uint64_t V, uint32_t *flags,
+                                                    uint64_t nwords) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords; w += warps) {
+        uint32_t word = 0;
+        for (int k = 0; k < 32; ++k) {
+            const uint64_t grp = 32 * w + (uint64_t)k;
+            bool ok = (grp + 1) * 128 <= T;
+            if (ok) {
+                const uint32_t *p = idx + 3 * (grp * 128 + 4 * (uint64_t)lane);
+                uint32_t x[12];
+                for (int c = 0; c < 12; ++c) x[c] = __ldg(p + c);
+                const uint64_t s0 = x[0], s1 = x[1];
+                ok = s0 + 2 < V && s1 + 2 < V && x[2] == s0 + 1 && x[3] == s0 + 1 && x[4] == s1 &&
+                     x[5] == s1 + 1 && x[6] == s0 + 1 && x[7] == s1 + 1 && x[8] == s0 + 2 && x[9] == s0 + 2 &&
+                     x[10] == s1 + 1 && x[11] == s1 + 2;
+            }
+            if (__all_sync(0xffffffffu, ok)) word |= 1u << k;
+        }
+        if (lane == 0) flags[w] = word;
+    }
+}
+
+cudaError_t launch_grid_flags(const uint32_t *idx, uint64_t T, uint64_t V, uint32_t *flags, uint64_t nwords,
+                              cudaStream_t s) {
+    if (nwords == 0) return cudaSuccess;
+    k_grid_flags<<<1024, 256, 0, s>>>(idx, T, V, flags, nwords);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_minmax_u32(const uint32_t *v, uint64_t n, unsigned *out2, cudaStream_t s) {
     k_minmax_u32<<<1024, 256, 0, s>>>(v, n, out2);
     return cudaGetLastError();

@@ -89,6 +89,9 @@ struct MeshDev {
     // 32-bit words); vertex i is fma(qpos[3i + a], step[a], lo[a]) in FP32
     const uint32_t *cidx;
     const uint16_t *qpos;
+    // bit G: 128-triangle group G is a row of a grid, whose index fields
+    // follow from its runs' first two (k_grid_flags); nullptr: none known
+    const uint32_t *gflag;
     uint32_t bits, mask, imin, pad;
     float lo[3], step[3];
     // texture of the textured resolve (Section 4.4): per-vertex uv (V x 2)

@@ -37,6 +37,9 @@ cudaError_t launch_aabb(const float *pos, uint64_t V, float *scratch, float *out
 cudaError_t launch_minmax_u32(const uint32_t *v, uint64_t n, unsigned *out2, cudaStream_t s);
 cudaError_t launch_pack_indices(const uint32_t *idx, uint64_t n, uint32_t imin, uint32_t bits, uint32_t *words,
                                 uint64_t nwords, cudaStream_t s);
+// grid flags of the 128-triangle groups of a mesh: ceil(ceil(T / 128) / 32) words
+cudaError_t launch_grid_flags(const uint32_t *idx, uint64_t T, uint64_t V, uint32_t *flags, uint64_t nwords,
+                              cudaStream_t s);
 cudaError_t launch_quantize_positions(const float *pos, uint64_t V, const double lo[3], const double size[3],
                                       uint16_t *q, cudaStream_t s);
 cudaError_t launch_count_diff(const uint64_t *a, const uint64_t *b, uint64_t n, unsigned long long *out,

@@ -70,6 +70,7 @@ struct MeshRec {
     bool comp = false;
     uint32_t *cidx = nullptr;
     uint16_t *qpos = nullptr;
+    uint32_t *gflag = nullptr;            // grid flags of the 128-triangle groups (k_grid_flags)
     uint64_t cwords = 0;
     uint32_t bits = 0, imin = 0;
     float clo[3] = {0, 0, 0}, cstep[3] = {0, 0, 0};
@@ -373,6 +374,7 @@ curast_status sync_scene(curast_ctx *c, cudaStream_t s) {
             if (r.comp) {
                 md[i].cidx = r.cidx;
                 md[i].qpos = r.qpos;
+                md[i].gflag = r.gflag;
                 md[i].bits = r.bits;
                 md[i].mask = r.bits >= 32 ? ~0u : (1u << r.bits) - 1u;
                 md[i].imin = r.imin;
@@ -780,8 +782,10 @@ int index_bits(uint32_t span) {
 void free_compressed(MeshRec &m) {
     if (m.cidx) cudaFree(m.cidx);
     if (m.qpos) cudaFree(m.qpos);
+    if (m.gflag) cudaFree(m.gflag);
     m.cidx = nullptr;
     m.qpos = nullptr;
+    m.gflag = nullptr;
 }
 
 // Section 4.6 encoding of an uploaded mesh into context-owned buffers (see
@@ -820,8 +824,18 @@ curast_status compress_mesh(curast_ctx *c, MeshRec &m) {
     }
     m.cidx = w;
     m.qpos = q;
+    const uint64_t gwords = ((m.T + 127) / 128 + 31) / 32;
+    if (gwords) {
+        e = cudaMalloc(reinterpret_cast<void **>(&m.gflag), gwords * sizeof(uint32_t));
+        if (e != cudaSuccess) {
+            m.gflag = nullptr;
+            free_compressed(m);
+            return e == cudaErrorMemoryAllocation ? CURAST_ERR_OUT_OF_MEMORY : CURAST_ERR_CUDA;
+        }
+    }
     cudaError_t e1 = cudaMemsetAsync(w, 0, m.cwords * sizeof(uint32_t), c->aux);
     if (e1 == cudaSuccess && m.T) e1 = launch_pack_indices(m.idx, 3 * m.T, imin, m.bits, w, m.cwords - 8, c->aux);
+    if (e1 == cudaSuccess && gwords) e1 = launch_grid_flags(m.idx, m.T, m.V, m.gflag, gwords, c->aux);
     if (e1 == cudaSuccess && m.V) e1 = launch_quantize_positions(m.pos, m.V, lo, size, q, c->aux);
     if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(c->aux);
     if (e1 != cudaSuccess) {
@@ -1015,6 +1029,7 @@ curast_status curast_get_mesh_info(const curast_ctx *c, uint32_t mesh_id, curast
         out->geometry_bytes = ((3 * m.T * m.bits + 31) >> 5) * 4 + 6 * m.V;
         out->packed_indices = m.cidx;
         out->quantized_positions = m.qpos;
+        out->grid_flags = m.gflag;
     } else {
         out->geometry_bytes = 12 * m.T + 12 * m.V;
     }

@@ -519,6 +519,55 @@ __device__ __forceinline__ void decode_pair(const MeshDev &mesh, const uint32_t 
     }
 }
 
+// The four triangles of a lane in strip order, (s0 s1 s2) (s2 s1 s3)
+// (s2 s3 s4) (s4 s3 s5) with sv = s0 .. s5: the six vertices loaded and
+// transformed once, each triangle culled from the bounds of its three.
+template <bool NEAR, bool COMP>
+__device__ __forceinline__ void strip_cull(const FastPair &fp, const MeshDev &mesh, const float *pos,
+                                           const uint32_t (&sv)[6], bool (&cull)[4]) {
+    // vertex pairs (s0, s1), (s2, s3), (s4, s5)
+    float2 X[3], Y[3], w[3], r[3];
+    if constexpr (!COMP) {
+        float v[18];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float *q = pos + 3 * (uint64_t)sv[c];
+            v[3 * c] = __ldg(q); v[3 * c + 1] = __ldg(q + 1); v[3 * c + 2] = __ldg(q + 2);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            xform2(fp, make_float2(v[6 * c], v[6 * c + 3]), make_float2(v[6 * c + 1], v[6 * c + 4]),
+                   make_float2(v[6 * c + 2], v[6 * c + 5]), X[c], Y[c], w[c], r[c]);
+    } else {
+        // the 16-bit values, converted exactly (as u16_to_float) and
+        // dequantized as fma(q, step, lo), two vertices a packed pair
+        uint32_t fb[18];   // bits of the floats 2^23 + value
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const uint16_t *src = mesh.qpos + 3 * (uint64_t)sv[c];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) fb[3 * c + a] = 0x4B000000u | (uint32_t)__ldg(src + a);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 p[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                p[a] = fma_x2(sub_x2(make_float2(__int_as_float(fb[6 * c + a]), __int_as_float(fb[6 * c + 3 + a])),
+                                     dup(8388608.0f)),
+                              dup(mesh.step[a]), dup(mesh.lo[a]));
+            xform2(fp, p[0], p[1], p[2], X[c], Y[c], w[c], r[c]);
+        }
+    }
+    // triangles (t0, t1) from the pairs (s0, s1), (s2, s3); (t2, t3) from (s2, s3), (s4, s5)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        cull_tail2<NEAR>(fp, strip_min(X[h], X[h + 1]), strip_max(X[h], X[h + 1]), strip_min(Y[h], Y[h + 1]),
+                         strip_max(Y[h], Y[h + 1]), strip_min(w[h], w[h + 1]),
+                         NEAR ? strip_max(w[h], w[h + 1]) : make_float2(0.0f, 0.0f),
+                         strip_max(r[h], r[h + 1]), cull[2 * h], cull[2 * h + 1]);
+}
+
 // Single-pair items of plain meshes, four consecutive triangles a lane: a
 // warp takes the 128-triangle groups g = warp, warp + 8, ... of the item and
 // lane l the triangles 128 g + 4 l .. 128 g + 4 l + 3, whose twelve index
@@ -544,100 +593,75 @@ __device__ __forceinline__ void cull_quads(const FrameDev &f, const uint32_t *id
     const float *pos = mesh.pos;
     for (uint32_t g = warp; g < 2 * tpt; g += kConsumerWarps) {   // the warp stays converged
         const uint32_t lt = 128 * g + 4 * lane;
-        uint32_t ix[12];
-        if constexpr (!COMP) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(idx + 3 * lt);
-            const uint4 ia = src[0], ib = src[1], ic = src[2];
-            ix[0] = ia.x; ix[1] = ia.y; ix[2] = ia.z; ix[3] = ia.w; ix[4] = ib.x; ix[5] = ib.y;
-            ix[6] = ib.z; ix[7] = ib.w; ix[8] = ic.x; ix[9] = ic.y; ix[10] = ic.z; ix[11] = ic.w;
-        } else {
-            // index 3 lt + k of the item sits at bit (3 lt + k) bits of the slot
-            uint32_t bit = 3 * lt * mesh.bits;
-#pragma unroll
-            for (int k = 0; k < 12; ++k, bit += mesh.bits)
-                ix[k] = mesh.imin + (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
-        }
-        const uint32_t smax = max(max(ix[0], max(ix[1], ix[2])), max(ix[5], max(ix[8], ix[11])));
-        const bool strip = (lt + 3 < d.n) & (all_valid | (smax < v32)) & (ix[3] == ix[2]) & (ix[4] == ix[1]) &
-                           (ix[6] == ix[2]) & (ix[7] == ix[5]) & (ix[9] == ix[8]) & (ix[10] == ix[5]);
         bool cull[4];
         bool valid[4] = {true, true, true, true};
-        if (__all_sync(0xffffffffu, strip)) {
-            const uint32_t sv[6] = {ix[0], ix[1], ix[2], ix[5], ix[8], ix[11]};
-            // vertex pairs (s0, s1), (s2, s3), (s4, s5)
-            float2 X[3], Y[3], w[3], r[3];
-            if constexpr (!COMP) {
-                float v[18];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    const float *q = pos + 3 * (uint64_t)sv[c];
-                    v[3 * c] = __ldg(q); v[3 * c + 1] = __ldg(q + 1); v[3 * c + 2] = __ldg(q + 2);
-                }
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    xform2(fp, make_float2(v[6 * c], v[6 * c + 3]), make_float2(v[6 * c + 1], v[6 * c + 4]),
-                           make_float2(v[6 * c + 2], v[6 * c + 5]), X[c], Y[c], w[c], r[c]);
-            } else {
-                // the 16-bit values, converted exactly (as u16_to_float) and
-                // dequantized as fma(q, step, lo), two vertices a packed pair
-                uint32_t q[18];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    const uint16_t *src = mesh.qpos + 3 * (uint64_t)sv[c];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) q[3 * c + a] = (uint32_t)__ldg(src + a);
-                }
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float2 p[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        p[a] = fma_x2(sub_x2(make_float2(__int_as_float(0x4B000000 | q[6 * c + a]),
-                                                         __int_as_float(0x4B000000 | q[6 * c + 3 + a])),
-                                             dup(8388608.0f)),
-                                      dup(mesh.step[a]), dup(mesh.lo[a]));
-                    xform2(fp, p[0], p[1], p[2], X[c], Y[c], w[c], r[c]);
-                }
-            }
-            // triangles (t0, t1) from the pairs (s0, s1), (s2, s3); (t2, t3) from (s2, s3), (s4, s5)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                cull_tail2<NEAR>(fp, strip_min(X[h], X[h + 1]), strip_max(X[h], X[h + 1]), strip_min(Y[h], Y[h + 1]),
-                                 strip_max(Y[h], Y[h + 1]), strip_min(w[h], w[h + 1]),
-                                 NEAR ? strip_max(w[h], w[h + 1]) : make_float2(0.0f, 0.0f),
-                                 strip_max(r[h], r[h + 1]), cull[2 * h], cull[2 * h + 1]);
+        bool grid = false;
+        if constexpr (COMP) {
+            // a group flagged as a grid row (k_grid_flags): the lane's first
+            // two index fields give the other ten
+            const uint64_t G = (d.t0 >> 7) + g;
+            grid = mesh.gflag != nullptr && ((__ldg(mesh.gflag + (G >> 5)) >> (G & 31u)) & 1u);
+        }
+        if (grid) {
+            uint32_t bit = 3 * lt * mesh.bits;
+            const uint32_t s0 = mesh.imin + (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
+            bit += mesh.bits;
+            const uint32_t s1 = mesh.imin + (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
+            const uint32_t sv[6] = {s0, s1, s0 + 1, s1 + 1, s0 + 2, s1 + 2};
+            strip_cull<NEAR, COMP>(fp, mesh, pos, sv, cull);
         } else {
+            uint32_t ix[12];
+            if constexpr (!COMP) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(idx + 3 * lt);
+                const uint4 ia = src[0], ib = src[1], ic = src[2];
+                ix[0] = ia.x; ix[1] = ia.y; ix[2] = ia.z; ix[3] = ia.w; ix[4] = ib.x; ix[5] = ib.y;
+                ix[6] = ib.z; ix[7] = ib.w; ix[8] = ic.x; ix[9] = ic.y; ix[10] = ic.z; ix[11] = ic.w;
+            } else {
+                // index 3 lt + k of the item sits at bit (3 lt + k) bits of the slot
+                uint32_t bit = 3 * lt * mesh.bits;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                valid[u] = lt + u < d.n;
-                if (valid[u] && !all_valid && max(ix[3 * u], max(ix[3 * u + 1], ix[3 * u + 2])) >= v32) {
-                    if (f.check) atomicOr(f.err, kErrIndex);
-                    valid[u] = false;
-                }
+                for (int k = 0; k < 12; ++k, bit += mesh.bits)
+                    ix[k] = mesh.imin + (__funnelshift_r(idx[bit >> 5], idx[(bit >> 5) + 1], bit & 31u) & mesh.mask);
             }
+            const uint32_t smax = max(max(ix[0], max(ix[1], ix[2])), max(ix[5], max(ix[8], ix[11])));
+            const bool strip = (lt + 3 < d.n) & (all_valid | (smax < v32)) & (ix[3] == ix[2]) & (ix[4] == ix[1]) &
+                               (ix[6] == ix[2]) & (ix[7] == ix[5]) & (ix[9] == ix[8]) & (ix[10] == ix[5]);
+            if (__all_sync(0xffffffffu, strip)) {
+                const uint32_t sv[6] = {ix[0], ix[1], ix[2], ix[5], ix[8], ix[11]};
+                strip_cull<NEAR, COMP>(fp, mesh, pos, sv, cull);
+            } else {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                Tri9 p[2];
-                if constexpr (COMP) {
-                    const uint32_t pix[2][3] = {{ix[6 * h], ix[6 * h + 1], ix[6 * h + 2]},
-                                                {ix[6 * h + 3], ix[6 * h + 4], ix[6 * h + 5]}};
-                    const bool pv[2] = {valid[2 * h], valid[2 * h + 1]};
-                    decode_pair(mesh, pix, pv, p);
-                } else
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    if (valid[2 * h + u]) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float *q = pos + 3 * (uint64_t)idx[3 * (lt + 2 * h + u) + c];   // (read again)
-                            p[u].v[3 * c] = __ldg(q); p[u].v[3 * c + 1] = __ldg(q + 1); p[u].v[3 * c + 2] = __ldg(q + 2);
-                        }
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
+                for (int u = 0; u < 4; ++u) {
+                    valid[u] = lt + u < d.n;
+                    if (valid[u] && !all_valid && max(ix[3 * u], max(ix[3 * u + 1], ix[3 * u + 2])) >= v32) {
+                        if (f.check) atomicOr(f.err, kErrIndex);
+                        valid[u] = false;
                     }
                 }
-                fast_cull2<NEAR>(fp, p[0], p[1], cull[2 * h], cull[2 * h + 1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    Tri9 p[2];
+                    if constexpr (COMP) {
+                        const uint32_t pix[2][3] = {{ix[6 * h], ix[6 * h + 1], ix[6 * h + 2]},
+                                                    {ix[6 * h + 3], ix[6 * h + 4], ix[6 * h + 5]}};
+                        const bool pv[2] = {valid[2 * h], valid[2 * h + 1]};
+                        decode_pair(mesh, pix, pv, p);
+                    } else
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (valid[2 * h + u]) {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const float *q = pos + 3 * (uint64_t)idx[3 * (lt + 2 * h + u) + c];   // (read again)
+                                p[u].v[3 * c] = __ldg(q); p[u].v[3 * c + 1] = __ldg(q + 1); p[u].v[3 * c + 2] = __ldg(q + 2);
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 9; ++c) p[u].v[c] = 0.0f;
+                        }
+                    }
+                    fast_cull2<NEAR>(fp, p[0], p[1], cull[2 * h], cull[2 * h + 1]);
+                }
             }
         }
         uint32_t nib = 0;

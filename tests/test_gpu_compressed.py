@@ -126,3 +126,72 @@ def test_compressed_mesh_limits(api):
     with pytest.raises(api.CurastError):
         r.upload_mesh(m.pos.cuda(), bad.cuda(), compressed=True)
     del keep
+
+
+def _grid_flags_expected(idx: np.ndarray, V: int) -> np.ndarray:
+    """The grid flags by their definition: group G of 128 triangles is set
+    when it lies wholly in the mesh and every run of four triangles of it is
+    the strip of two grid rows, (s0 s1 s2) (s2 s1 s3) (s2 s3 s4) (s4 s3 s5)
+    with s2 = s0 + 1, s4 = s0 + 2, s3 = s1 + 1, s5 = s1 + 2, all below V."""
+    T = idx.shape[0]
+    ng = (T + 127) // 128
+    words = np.zeros((ng + 31) // 32, np.uint32)
+    x = idx.astype(np.int64)
+    for G in range(T // 128):
+        r = x[128 * G:128 * G + 128].reshape(32, 12)
+        s0, s1 = r[:, 0], r[:, 1]
+        pat = np.stack([s0, s1, s0 + 1, s0 + 1, s1, s1 + 1, s0 + 1, s1 + 1, s0 + 2, s0 + 2, s1 + 1, s1 + 2], 1)
+        if np.array_equal(r, pat) and (s0 + 2 < V).all() and (s1 + 2 < V).all():
+            words[G // 32] |= np.uint32(1 << (G % 32))
+    return words
+
+
+def _grid_meshes():
+    """Grid meshes whose 128-triangle groups are all, some or none grid rows:
+    an even row of 96 cells (every group), an odd row of 97 cells (groups
+    whose runs straddle two rows are not), the 96-cell grid in shuffled
+    triangle order (none), and the 96-cell grid with one triangle of group 5
+    stretched to a far vertex (every group but that one)."""
+    a = S.heightfield_mesh(96, seed=5)
+    b = S.heightfield_mesh(97, seed=6)
+    g = torch.Generator().manual_seed(7)
+    c = S.Mesh(pos=a.pos.clone(), idx=a.idx[torch.randperm(a.T, generator=g)].contiguous(), rgba8=a.rgba8.clone(),
+               aabb=a.aabb)
+    d_idx = a.idx.clone()
+    d_idx[5 * 128 + 9, 2] = a.V - 1
+    d = S.Mesh(pos=a.pos.clone(), idx=d_idx, rgba8=a.rgba8.clone(), aabb=a.aabb)
+    return [a, b, c, d]
+
+
+def test_grid_flags_follow_their_definition(api):
+    meshes = _grid_meshes()
+    r = api.Renderer(0)
+    keep = [(m.pos.cuda(), m.idx.cuda(), m.rgba8.cuda()) for m in meshes]
+    for p, i, c in keep:
+        r.upload_mesh(p, i, c, compressed=True)
+    got = []
+    for k, m in enumerate(meshes):
+        info = r.mesh_info(k)
+        exp = _grid_flags_expected(m.idx.numpy().view(np.uint32), m.V)
+        words = _device_words(info["grid_flags"], exp.size, "<u4")
+        np.testing.assert_array_equal(words, exp, err_msg=f"mesh {k}")
+        got.append(int(np.unpackbits(exp.view(np.uint8)).sum()))
+    ng = [(m.T + 127) // 128 for m in meshes]
+    assert got[0] == ng[0] and 0 < got[1] < ng[1] and got[2] == 0 and got[3] == ng[3] - 1
+    del keep
+
+
+def test_grid_groups_render_as_decoded_oracle(api):
+    """Each mesh of _grid_meshes alone (single-pair frames, so the strip cull
+    of compressed meshes runs), seen from above and obliquely: bit-exact
+    against the oracle on the decoded mesh."""
+    for k, m in enumerate(_grid_meshes()):
+        sc = S.Scene(meshes=[m], instances=[S.Instance(0, np.eye(4, dtype=np.float32))])
+        for eye, target in (((0.5, 1.4, 0.5), (0.5, 0.0, 0.501)), ((-0.4, 0.6, -0.3), (0.5, 0.05, 0.5))):
+            cam = S.Camera(S.look_at(eye, target), S.perspective(60.0, 320 / 240, 1e-3, 100.0), 320, 240)
+            r = api.Renderer(0)
+            keep = upload(r, sc, compressed={0})
+            vis = r.render(cam.view, cam.proj, cam.W, cam.H)
+            r.sync()
+            assert_vis_equal(vis, oracle_vis(decoded_scene(sc, {0}), cam), f"mesh {k}")
+            del keep
