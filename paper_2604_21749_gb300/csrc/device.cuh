@@ -399,7 +399,12 @@ __device__ __forceinline__ bool pixel_key(const SubTri &s, int x, int y, uint64_
 // evaluated at the thread's first pixel and then stepped exactly: a step of
 // `stride` pixels is q rows and r columns (stride = q w + r), one column
 // changes E_k by -256 dy_k and one row by +256 dx_k, and a column past x1
-// wraps to the next row.
+// wraps to the next row.  U > 1: U pixels at a time -- their words first,
+// then the reads of the stored words all in flight together, then the
+// atomic minimums (their order does not change the result); stage 2, a warp
+// per triangle, waits on those reads (U = 4 there), while stage 3's blocks
+// and the overflow paths run faster one pixel at a time (U = 1).
+template <int U = 1>
 __device__ __forceinline__ void raster_range(const SubTri &s, int x0, int x1, int y0, int y1, int start, int stride,
                                              uint64_t *vis, int W) {
     const int w = x1 - x0 + 1;
@@ -419,17 +424,45 @@ __device__ __forceinline__ void raster_range(const SubTri &s, int x0, int x1, in
     const int64_t R0 = 256 * (dx0 + (int64_t)w * dy0), R1 = 256 * (dx1 + (int64_t)w * dy1),
                   R2 = 256 * (dx2 + (int64_t)w * dy2);
     const int64_t b0 = s.bias & 1u, b1 = (s.bias >> 1) & 1u, b2 = (s.bias >> 2) & 1u;
-    for (int64_t i = start; i < n; i += stride) {
-        if (((E0 - b0) | (E1 - b1) | (E2 - b2)) >= 0)
-            depth_test_write(vis, (size_t)y * (size_t)W + (size_t)x, frag_key(E0, E1, E2, s.A, s.iz, s.id));
-        x += r;
-        y += q;
-        E0 += S0; E1 += S1; E2 += S2;
-        if (x > x1) {
-            x -= w;
-            ++y;
-            E0 += R0; E1 += R1; E2 += R2;
+    if (U == 1) {
+        for (int64_t i = start; i < n; i += stride) {
+            if (((E0 - b0) | (E1 - b1) | (E2 - b2)) >= 0)
+                depth_test_write(vis, (size_t)y * (size_t)W + (size_t)x, frag_key(E0, E1, E2, s.A, s.iz, s.id));
+            x += r;
+            y += q;
+            E0 += S0; E1 += S1; E2 += S2;
+            if (x > x1) {
+                x -= w;
+                ++y;
+                E0 += R0; E1 += R1; E2 += R2;
+            }
         }
+        return;
+    }
+    for (int64_t i = start; i < n; i += U * (int64_t)stride) {
+        uint64_t key[U];
+        unsigned long long *px[U];
+        bool cov[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cov[u] = i + u * (int64_t)stride < n && ((E0 - b0) | (E1 - b1) | (E2 - b2)) >= 0;
+            px[u] = reinterpret_cast<unsigned long long *>(vis + (size_t)y * (size_t)W + (size_t)x);
+            key[u] = cov[u] ? frag_key(E0, E1, E2, s.A, s.iz, s.id) : 0ull;
+            x += r;
+            y += q;
+            E0 += S0; E1 += S1; E2 += S2;
+            if (x > x1) {
+                x -= w;
+                ++y;
+                E0 += R0; E1 += R1; E2 += R2;
+            }
+        }
+        unsigned long long old[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) old[u] = cov[u] ? __ldcg(px[u]) : 0ull;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (cov[u] && key[u] < old[u]) atomicMin(px[u], (unsigned long long)key[u]);
     }
 }
 

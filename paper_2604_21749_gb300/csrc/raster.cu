@@ -348,7 +348,14 @@ __global__ void __launch_bounds__(256) k_stage2(FrameDev f) {
         CV c[3];
         load_clip(f, mesh, e.pair, e.id - pr.base, vw, c);
         CV poly[kMaxPoly];
-        const int np = clip_polygon(c, vw.nearv, poly);
+        int np;
+        if ((outcode(c[0], vw.nearv) | outcode(c[1], vw.nearv) | outcode(c[2], vw.nearv)) == 0) {
+            // inside every plane: Sutherland-Hodgman would return it unchanged
+            poly[0] = c[0]; poly[1] = c[1]; poly[2] = c[2];
+            np = 3;
+        } else {
+            np = clip_polygon(c, vw.nearv, poly);
+        }
         if (np < 3) continue;
         int X[kMaxPoly], Y[kMaxPoly];
         float iz[kMaxPoly];
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(256) k_stage2(FrameDev f) {
             if (!setup_subtri(s, vw.W, vw.H)) continue;
             const int64_t cnt = (int64_t)(s.x1 - s.x0 + 1) * (int64_t)(s.y1 - s.y0 + 1);
             if (cnt <= (int64_t)f.s2_max) {
-                raster_range(s, s.x0, s.x1, s.y0, s.y1, lane, 32, vw.vis, vw.W);
+                raster_range<4>(s, s.x0, s.x1, s.y0, s.y1, lane, 32, vw.vis, vw.W);
                 n_s2 += (lane == 0);
             } else {
                 const int tl = (int)f.tile_log2;
