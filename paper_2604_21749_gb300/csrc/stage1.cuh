@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(s1::kThreads, (FUSED || INST) ? 3 : s1::kCullB
         }
         const Desc d = S.desc[slot];
         if (d.b >= rd.b1) break;
-        const MeshDev mesh = S.mesh[slot];
+        const MeshDev &mesh = S.mesh[slot];   // read in place: the slot is ours until we release it
         const uint32_t *idx = S.idx[slot];
         // index bound as a 32-bit compare: every uint32 index is below V >= 2^32
         const bool all_valid = mesh.V > 0xFFFFFFFFull;
