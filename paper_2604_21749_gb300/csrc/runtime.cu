@@ -204,11 +204,16 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     const double kb = F * u * 7.002 * S[2];
     const double kc = 1.01 * (rho + 7.01 * u);
     const double kd = 1.01 * (5.01 * u * (std::max(hw, hh) + 1) + rho + 7.01 * u) + 1.0 / 512;
-    const double win = 8.0 * std::min(hw, hh);
-    // raise wsafe until the margin stays below 1/2 pixel wherever the test
-    // applies (w > wsafe, |X'|, |Y'| < win; the reciprocal may read 1 + rho
-    // high), which the error analysis assumes and the kernel relies on
-    const double room = 0.5 - kc * win - kd;
+    // The test applies where w > wsafe and |X'|, |Y'| < win = 100 min(W/2,
+    // H/2).  wsafe is raised until the margin stays below 20 min(W/2, H/2)
+    // there (the reciprocal may read 1 + rho high), so every exact vertex of a
+    // tested triangle has |X'|, |Y'| < 120 min(W/2, H/2): well inside the
+    // guard band (|X - W/2| <= 128 W/2, likewise for Y), where the exact path
+    // snaps it and never clips.  The bound is linear in |X'| and holds at any
+    // size of the margin; a margin of many pixels only culls less.
+    const double hm = std::min(hw, hh);
+    const double win = 100.0 * hm;
+    const double room = 20.0 * hm - kc * win - kd;
     if (!(room > 0.0)) return;
     ws = std::max(ws, 1.01 * (1 + rho) * (ka + kb * win) / room);
     if (!std::isfinite(ka) || !std::isfinite(ws) || ka > 1e30 || ws > 1e30) return;
@@ -224,9 +229,6 @@ void fast_constants(PairDev &p, const MeshRec &m, const ViewDev &v) {
     p.fs[1] = (float)(std::ldexp(ay * S[1] + by * S[2], -19) * (1 + 1e-6));
     p.fs[2] = (float)(std::ldexp(S[2], -19) * (1 + 1e-6));
     p.wsafe = (float)(ws * (1 + 1e-6));
-    // inside |X'|, |Y'| < 8 min(W/2, H/2) every vertex lies far within the
-    // guard band (|X - W/2| <= 128 W/2, likewise for Y), so the exact path
-    // would not clip it
     p.win = (float)win;
 }
 

@@ -83,7 +83,8 @@ struct Tri9 { float v[9]; };    // the three vertices of a triangle
 // Evaluated without branches.
 __device__ __forceinline__ bool fast_cull(const FastPair &fp, const Tri9 &p) {
     // vertex by vertex into running bounds (few live registers); the host
-    // chose wsafe so that every w > wsafe keeps the margin m below 1/2
+    // chose wsafe so that every w > wsafe keeps each exact vertex of a
+    // tested triangle inside the guard band (no clipping in the exact path)
     float xmn, xmx, ymn, ymx, wmn, wmx, rmx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {

@@ -62,8 +62,8 @@ def _constants(mv, lo, hi, cp, W, H):
     ka, kb = F * U * max(kax, kay), F * U * 7.002 * Sr[2]
     kc = 1.01 * (RHO + 7.01 * U)
     kd = 1.01 * (5.01 * U * (max(hw, hh) + 1) + RHO + 7.01 * U) + 1.0 / 512
-    win = 8.0 * min(hw, hh)
-    room = 0.5 - kc * win - kd
+    win = 100.0 * min(hw, hh)
+    room = 20.0 * min(hw, hh) - kc * win - kd
     if not room > 0:
         return None
     ws = max(ws, 1.01 * (1 + RHO) * (ka + kb * win) / room)
@@ -145,7 +145,9 @@ def test_triangle_margin_holds_exact_snapped_vertices(setup):
         X, Y = _f32(xw * r), _f32(yw * r)
         a = np.maximum(np.abs(X), np.abs(Y))
         m = _fma(r, _fma(k[1], a, k[0]), _fma(k[2], a, k[3])).astype(np.float64)
-        ok = (w > ws) & (a < win) & inside
+        ok = (w > ws) & (a < win)
+        # the premise of the bound: every tested vertex is snapped unclipped
+        assert inside[ok].all(), "a tested vertex lies outside the guard band in the exact path"
         err = np.maximum(np.abs(X - Xe), np.abs(Y - Ye))
         applied += int(ok.sum())
         if ok.any():
@@ -198,7 +200,8 @@ def test_group_margin_holds_exact_snapped_vertices(setup):
         a = np.maximum(_f32(np.abs(X0) + hx), _f32(np.abs(Y0) + hy))
         m = (_f32(F32(2.0) * _fma(rh, _fma(k[1], a, k[0]), _fma(k[2], a, k[3])))
              + _f32(F32(2.0) * _f32(hx + hy) * F32(4.0e-6))).astype(np.float64)
-        ok = (wl > ws) & (a < win) & inside.all(axis=1)
+        ok = (wl > ws) & (a < win)
+        assert inside[ok].all(), "a tested group holds a vertex outside the guard band in the exact path"
         exc = np.maximum.reduce([(X0 - hx)[:, None] - Xe, Xe - (X0 + hx)[:, None],
                                  (Y0 - hy)[:, None] - Ye, Ye - (Y0 + hy)[:, None]]).max(axis=1)
         exc = np.maximum(exc, 0.0)
