@@ -357,7 +357,7 @@ constexpr int kConsumers = 32 * kConsumerWarps;      // 256 consumer threads
 constexpr int kThreads = kConsumers + 32;            // + one producer warp
 constexpr int kMaxTpt = 4;                           // triangles per consumer per item
 constexpr int kItem = kConsumers * kMaxTpt;          // 1024 triangles, 12 KB of index triples
-constexpr int kSlots = 3;
+constexpr int kSlots = 4;
 constexpr int kQueue = 64;                           // per-warp survivors (fused kernel)
 constexpr int kMaxPairs = 64;                        // pairs of one segment (pairs_per_segment <= 64)
 constexpr int kNT = 2;                               // triangles a lane loads together
