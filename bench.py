@@ -457,25 +457,32 @@ def run_ours(args, ranks: Ranks):
     return result
 
 
-def thirty_tiles_frame(args, sc, cam, dev, stream):
-    """The same layout with only the 30 tiles wholly inside the view that lie
-    nearest its centre (30 x 2 x 4096^2 = 1.007 B triangles, every one of them
-    in the frustum): frame ms, Gtris/s, stage ms and the cull's roofline."""
+def tiles_wholly_in_view(cam, tiles: int, count: int = 30, height: float = 0.2):
+    """The `count` tiles of the tiles x tiles layout (tile k spans x in [i, i+1],
+    z in [j, j+1], y in [0, height]) whose 8 box corners all project in front
+    of the camera and inside the viewport, nearest the layout's centre first."""
     import numpy as np
-    import torch
-    from paper_2604_21749_gb300 import api
     V = np.asarray(cam.view, np.float64)
     P = np.asarray(cam.proj, np.float64)
     inside = []
-    for k in range(args.tiles * args.tiles):
-        i, j = k % args.tiles, k // args.tiles
-        c = np.array([[i + a, y, j + b, 1.0] for a in (0, 1) for b in (0, 1) for y in (0.0, 0.2)])
+    for k in range(tiles * tiles):
+        i, j = k % tiles, k // tiles
+        c = np.array([[i + a, y, j + b, 1.0] for a in (0, 1) for b in (0, 1) for y in (0.0, height)])
         h = (P @ V @ c.T).T
         w = h[:, 3]
         if (w > 0).all() and (np.abs(h[:, 0] / w) <= 1).all() and (np.abs(h[:, 1] / w) <= 1).all():
             inside.append(k)
-    cx = cz = args.tiles / 2.0
-    keep = sorted(inside, key=lambda k: (k % args.tiles + 0.5 - cx) ** 2 + (k // args.tiles + 0.5 - cz) ** 2)[:30]
+    cx = cz = tiles / 2.0
+    return sorted(inside, key=lambda k: (k % tiles + 0.5 - cx) ** 2 + (k // tiles + 0.5 - cz) ** 2)[:count]
+
+
+def thirty_tiles_frame(args, sc, cam, dev, stream):
+    """The same layout with only the 30 tiles wholly inside the view that lie
+    nearest its centre (30 x 2 x 4096^2 = 1.007 B triangles, every one of them
+    in the frustum): frame ms, Gtris/s, stage ms and the cull's roofline."""
+    import torch
+    from paper_2604_21749_gb300 import api
+    keep = tiles_wholly_in_view(cam, args.tiles)
     r = api.Renderer(dev.index)
     for n, k in enumerate(keep):
         m = sc.meshes[k]
