@@ -584,7 +584,10 @@ __device__ __forceinline__ void strip_cull(const FastPair &fp, const MeshDev &me
 // triangles 128 g + 32 h + b at bit b), gathered by OR-reductions and stored
 // at once.  Compressed meshes (COMP, Section 4.6) decode the twelve index
 // fields of a lane from the packed bits, and in strip order only the six
-// vertices' 16-bit positions.
+// vertices' 16-bit positions; in a group their grid flag marks as two grid
+// rows, only the first two fields (s0, s1) are decoded and the strip check is
+// skipped.  The mesh record is read in place in the item's shared-memory
+// slot, which stays the warp's until it releases the slot.
 template <bool NEAR, bool COMP>
 __device__ __forceinline__ void cull_quads(const FrameDev &f, const uint32_t *idx, const FastPair &fp,
                                            const MeshDev &mesh, const s1::Desc &d, uint32_t tpt, int warp, int lane) {
