@@ -146,8 +146,10 @@ def test_triangle_margin_holds_exact_snapped_vertices(setup):
         a = np.maximum(np.abs(X), np.abs(Y))
         m = _fma(r, _fma(k[1], a, k[0]), _fma(k[2], a, k[3])).astype(np.float64)
         ok = (w > ws) & (a < win)
-        # the premise of the bound: every tested vertex is snapped unclipped
+        # the premise of the bound: every tested vertex is snapped unclipped,
+        # which the host secures by keeping the margin below 20 min(W/2, H/2)
         assert inside[ok].all(), "a tested vertex lies outside the guard band in the exact path"
+        assert (m[ok] < 20.0 * min(cam.W, cam.H) / 2.0).all()
         err = np.maximum(np.abs(X - Xe), np.abs(Y - Ye))
         applied += int(ok.sum())
         if ok.any():
