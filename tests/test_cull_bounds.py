@@ -124,18 +124,17 @@ def _exact(mv, cp, cam, pts):
     return Xe.reshape(pts.shape[:-1]), Ye.reshape(pts.shape[:-1]), inside.reshape(pts.shape[:-1])
 
 
-@pytest.mark.parametrize("setup", SETUPS, ids=[s[-1] for s in SETUPS])
-def test_triangle_margin_holds_exact_snapped_vertices(setup):
-    """Per vertex: the estimate X'~ = (X'w) * rcp(w) from the FMA rows and the
-    exact snapped X' differ by less than m = max(1/w)(ka + kb a) + kc a + kd
-    wherever the test applies (w > wsafe, |X'|, |Y'| < window)."""
+def _vertex_margin_worst(setup, kscale=1.0, n=60000):
+    """Largest ratio of the exact snapped vertex's distance from its estimate
+    to the margin m (scaled by kscale) over sampled mesh points where the
+    test applies, and the number of such samples (both rcp directions)."""
     cam, model, lo, hi, _ = setup
     cp = orc.camera_params(np.asarray(cam.proj, np.float32))
     mv = orc.model_view(np.asarray(cam.view, np.float32), model)
     c = _constants(mv, lo, hi, cp, cam.W, cam.H)
     assert c is not None
     rows, k, ws, win, _ = c
-    pts = np.random.default_rng(11).uniform(lo, hi, size=(60000, 3)).astype(F32)
+    pts = np.random.default_rng(11).uniform(lo, hi, size=(n, 3)).astype(F32)
     Xe, Ye, inside = _exact(mv, cp, cam, pts)
     x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
     xw, yw, w = _row(rows[0], x, y, z), _row(rows[1], x, y, z), _row(rows[2], x, y, z)
@@ -144,7 +143,7 @@ def test_triangle_margin_holds_exact_snapped_vertices(setup):
         r = _rcp(w, s)
         X, Y = _f32(xw * r), _f32(yw * r)
         a = np.maximum(np.abs(X), np.abs(Y))
-        m = _fma(r, _fma(k[1], a, k[0]), _fma(k[2], a, k[3])).astype(np.float64)
+        m = _fma(r, _fma(k[1], a, k[0]), _fma(k[2], a, k[3])).astype(np.float64) * kscale
         ok = (w > ws) & (a < win)
         # the premise of the bound: every tested vertex is snapped unclipped,
         # which the host secures by keeping the margin below 20 min(W/2, H/2)
@@ -154,8 +153,24 @@ def test_triangle_margin_holds_exact_snapped_vertices(setup):
         applied += int(ok.sum())
         if ok.any():
             worst = max(worst, float((err[ok] / m[ok]).max()))
+    return worst, applied
+
+
+@pytest.mark.parametrize("setup", SETUPS, ids=[s[-1] for s in SETUPS])
+def test_triangle_margin_holds_exact_snapped_vertices(setup):
+    """Per vertex: the estimate X'~ = (X'w) * rcp(w) from the FMA rows and the
+    exact snapped X' differ by less than m = max(1/w)(ka + kb a) + kc a + kd
+    wherever the test applies (w > wsafe, |X'|, |Y'| < window)."""
+    worst, applied = _vertex_margin_worst(setup)
     assert applied > 0
     assert worst < 1.0, f"an exact snapped vertex lies {worst:.3f} margins from its estimate"
+
+
+def test_a_margin_a_quarter_too_small_is_caught():
+    """The check is sharp: with the margin constants scaled by 1/4 some exact
+    snapped vertex falls outside its widened estimate."""
+    worst = max(_vertex_margin_worst(s, kscale=0.25, n=20000)[0] for s in SETUPS)
+    assert worst > 1.0
 
 
 @pytest.mark.parametrize("setup", SETUPS, ids=[s[-1] for s in SETUPS])
